@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Throughput and latency of the CMA-ES silhouette tracker on one GB300.
+
+Metric: candidate pose evaluations per second (render + loss) at 640x512 with
+populations of lam = 64, and the p99 per-frame latency.  Workload (synthetic,
+seeded): the 4-link instrument with a ~20k-triangle procedural mesh, fx = fy =
+800, a sinusoidal 30 Hz trajectory, observed masks = render at the true state
+with occluding ellipses (10-30 % of the tool) and 2 % pixel flips; every step is
+one tracked frame = 5 CMA-ES generations of 64 candidates warm-started from the
+previous frame, loss 1 - IoU.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank tracks its own camera stream (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2603_11404_gb300 import workload as wl  # noqa: E402
+
+METRIC = "candidate pose evals/sec (render+loss) at 640x512, λ=64; p99 frame latency"
+UNIT = "evals/s"
+LAM, GENS = 64, 5
+SEED = 2000
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+ALGO_OPS_PER_VERT, ALGO_OPS_PER_TRI, ALGO_OPS_PER_BBOX_PX = 16, 40, 4
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=300)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--cpu-seconds", type=float, default=10.0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _workload(rank: int, n_frames: int):
+    sc = wl.make_scene("c2", "c2")
+    rng = np.random.default_rng(SEED + 7919 * rank)
+    gt0 = wl.sample_state(rng, sc.K)
+    traj = wl.sinusoidal_trajectory(rng, gt0, n_frames)
+    init = gt0 + rng.normal(size=9) * wl.default_scales(9)
+    return sc, traj, init
+
+
+def _corrupt(S, rank, f):
+    return wl.corrupt_mask(S, np.random.default_rng((SEED + 7919 * rank) * 100003 + f))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2603_11404_gb300 import api, build
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl")
+    build.build()
+    n_frames = a.warmup + a.steps
+    sc, traj, init = _workload(rank, n_frames)
+    W, H = sc.K.width, sc.K.height
+    tr = api.Tracker(sc, loss_kind=wl.LOSS_ONE_MINUS_IOU, lambda_max=LAM)
+
+    # observed masks: library render at the true state, corrupted on the host
+    masks = np.zeros((n_frames, H, W), np.uint8)
+    for f in range(n_frames):
+        S = api.unpack_mask(tr.render(torch.from_numpy(traj[f].astype(np.float32)).cuda()), W).cpu().numpy()
+        masks[f] = _corrupt(S, rank, f)
+    masks_dev = torch.from_numpy(masks).cuda()
+    packed = torch.stack([tr.pack_mask(masks_dev[f]) for f in range(n_frames)])
+    masks_pinned = torch.from_numpy(masks).pin_memory()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    scales = wl.default_scales(9)
+    stream = torch.cuda.current_stream()
+
+    # ---- value: device-resident masks, CUDA-event time per tracked frame ----
+    es = api.CMAES(tr, LAM, init, scales, sigma0=1.0, seed=SEED + rank)
+    poses = torch.empty((n_frames, 9), dtype=torch.float32, device="cuda")
+    for f in range(a.warmup):
+        es.track_frame(packed[f], GENS, pose_out=poses[f])
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for i in range(a.steps):
+            f = a.warmup + i
+            flush.fill_(i)
+            evs[i][0].record(stream)
+            es.track_frame(packed[f], GENS, pose_out=poses[f])
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+    step_ms = np.array([s.elapsed_time(e) for s, e in evs])
+    total_s = float(step_ms.sum()) / 1e3
+    if ws > 1:
+        t = torch.tensor([total_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+        dist.barrier()
+    evals = ws * a.steps * LAM * GENS
+    value = evals / total_s
+    pose_err = np.abs(poses[a.warmup:].cpu().numpy() - traj[a.warmup:].astype(np.float32))
+
+    # ---- e2e: the public host call (mask H2D from pinned memory, pose D2H) ----
+    es2 = api.CMAES(tr, LAM, init, scales, sigma0=1.0, seed=SEED + rank)
+    for f in range(a.warmup):
+        es2.track_frame_host(masks_pinned[f], GENS)
+    e2e_ms = []
+    for i in range(a.steps):
+        f = a.warmup + i
+        flush.fill_(i)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        es2.track_frame_host(masks_pinned[f], GENS)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_total = sum(e2e_ms) / 1e3
+    if ws > 1:
+        t = torch.tensor([e2e_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+
+    # ---- dominant kernel: the fused fitness launch on this run's populations ----
+    R = min(100, a.steps)
+    pops = []
+    es3 = api.CMAES(tr, LAM, init, scales, sigma0=1.0, seed=SEED + rank + 17)
+    for i in range(R):
+        f = a.warmup + i
+        es3.reset(poses[f].double().cpu().numpy())
+        pops.append(es3.ask())
+    loss_buf = torch.empty(LAM, dtype=torch.float32, device="cuda")
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(R)]
+    for i in range(R):
+        flush.fill_(i)
+        kev[i][0].record(stream)
+        tr.eval_population(pops[i], packed[a.warmup + i], loss=loss_buf)
+        kev[i][1].record(stream)
+    torch.cuda.synchronize()
+    k_ms = np.array([s.elapsed_time(e) for s, e in kev])
+    # algorithmic work of those launches: 16 ops/vertex, 40 ops/live triangle,
+    # 4 ops per pixel of each triangle's screen-clipped bounding box
+    ops = 0.0
+    for i in range(0, R, max(1, R // 10)):
+        _, cnt, snap, _ = tr.eval_population_debug(pops[i], packed[a.warmup + i])
+        ops += _algo_ops(sc, snap) * (R / len(range(0, R, max(1, R // 10))))
+    ops_per_launch = ops / R
+    achieved = ops_per_launch / (float(k_ms.mean()) / 1e3)
+    peak = _alu_peak()
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "k_eval (fused FK/projection/snap + raster + popcount)",
+                "kernel_ms": float(k_ms.mean()), "ops_per_launch": ops_per_launch,
+                "peak_source": "152 SMs x 64 INT32 ALU lanes/clk x 2070 MHz (derived; LOP3 probe 20.0 Tops/s)"}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": total_s * 1e3 / a.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": "640x512 tracking: 4-link instrument, %d-triangle procedural mesh, fx=fy=800, "
+                               "lambda=64, 5 CMA-ES generations per frame warm-started, loss 1-IoU, corrupted "
+                               "masks (ellipses 10-30%%, 2%% flips), sinusoidal 30 Hz trajectory" % sc.n_tris,
+                   "global_batch": LAM * ws, "image": "640x512", "generations_per_frame": GENS,
+                   "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{ws}"},
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                       "e2e_p50": float(np.percentile(e2e_ms, 50)), "e2e_p99": float(np.percentile(e2e_ms, 99))},
+        "e2e": {"value": evals / e2e_total, "unit": UNIT, "h2d_bytes_per_step": H * W,
+                "d2h_bytes_per_step": 9 * 4 + 4},
+        "gpu_launches": a.steps * (2 + 3 * GENS),
+        "roofline": roofline,
+        "tracking_error": {"rot_rad_median": float(np.median(pose_err[:, :3])),
+                           "trans_mm_median": float(np.median(pose_err[:, 3:6])),
+                           "joint_median": float(np.median(pose_err[:, 6:]))},
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and ws == 1 and not a.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(a.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def _algo_ops(sc, snap):
+    """16 ops per vertex + 40 per live triangle + 4 per pixel of every live
+    triangle's screen-clipped bounding box, summed over the population."""
+    import torch
+    _, tris, _ = sc.flat()
+    t = torch.from_numpy(tris.astype(np.int64)).to(snap.device)
+    W, H = sc.K.width, sc.K.height
+    xs = snap[:, :, 0].long()[:, t]  # [lam, T, 3]
+    ys = snap[:, :, 1].long()[:, t]
+    live = (xs != np.iinfo(np.int32).min).all(dim=2)
+    j0 = torch.clamp(torch.div(xs.min(2).values + 255, 256, rounding_mode="floor"), min=0)
+    j1 = torch.clamp(torch.div(xs.max(2).values, 256, rounding_mode="floor"), max=W - 1)
+    i0 = torch.clamp(torch.div(ys.min(2).values + 255, 256, rounding_mode="floor"), min=0)
+    i1 = torch.clamp(torch.div(ys.max(2).values, 256, rounding_mode="floor"), max=H - 1)
+    area = torch.clamp(j1 - j0 + 1, min=0) * torch.clamp(i1 - i0 + 1, min=0) * live
+    n_v = snap.shape[0] * snap.shape[1]
+    return float(ALGO_OPS_PER_VERT * n_v + ALGO_OPS_PER_TRI * live.sum().item()
+                 + ALGO_OPS_PER_BBOX_PX * area.sum().item())
+
+
+def _alu_peak():
+    """INT32 ALU-pipe issue rate: 152 SMs x 64 lanes/clk (4 SMSPs x 16) x 2070 MHz."""
+    return 152 * 64 * 2.07e9
+
+
+def cpu_baseline(seconds: float):
+    """The CPU oracle as it stands, on this host's cores, for a bounded sample."""
+    import oracle
+    sc, traj, init = _workload(0, 64)
+    cores = len(os.sched_getaffinity(0))
+    rng = np.random.default_rng(99)
+    n, t0, f = 0, time.perf_counter(), 0
+    while True:
+        M = _corrupt(oracle.render(sc, traj[f % 64]), 0, f % 64)
+        P = wl.population_around(rng, traj[f % 64], LAM)
+        t1 = time.perf_counter()
+        oracle.eval_population(sc, P, M, n_threads=cores)
+        n += LAM
+        f += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    el = time.perf_counter() - t0
+    return {"value": n / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{f} populations of {LAM} candidates (640x512, {sc.n_tris} triangles), "
+                      f"oracle renderer + counts over {cores} threads, {el:.1f} s incl. mask setup"}
+
+
+def run_reference(a):
+    """The oracle tracker (FP64 CMA-ES + exact CPU renderer) as the reference arm."""
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    import oracle
+    from oracle.cmaes import CMAES
+    from oracle.tracker import track_frame
+    cores = len(os.sched_getaffinity(0))
+    n_frames = a.warmup + a.steps
+    sc, traj, init = _workload(0, n_frames)
+    es = CMAES(9, LAM, init, wl.default_scales(9), sigma0=1.0, seed=SEED)
+    est = init.copy()
+    times = []
+    budget = 120.0
+    t_start = time.perf_counter()
+    done = 0
+    for f in range(n_frames):
+        M = _corrupt(oracle.render(sc, traj[f]), 0, f)
+        t0 = time.perf_counter()
+        est, _ = track_frame(es, sc, M, GENS, wl.LOSS_ONE_MINUS_IOU, est, n_threads=cores)
+        if f >= a.warmup:
+            times.append(time.perf_counter() - t0)
+            done += 1
+        if time.perf_counter() - t_start > budget and done >= 1:
+            break
+    total = sum(times)
+    value = done * LAM * GENS / total
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": done,
+           "warmup": a.warmup, "ms_per_step": total * 1e3 / done, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64+int64", "data": "synthetic",
+           "config": {"workload": "640x512 tracking (same as ours), oracle tracker", "global_batch": LAM,
+                      "image": "640x512", "generations_per_frame": GENS},
+           "latency_ms": {"p50": float(np.percentile(times, 50) * 1e3), "p99": float(np.percentile(times, 99) * 1e3)},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"{done} tracked frames x {GENS} generations x {LAM} candidates"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    args = _args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)

@@ -1,0 +1,264 @@
+/*
+ * tracker.h -- C ABI of the GB300 (sm_103a) silhouette-fitness library for the
+ * CMA-ES surgical-instrument tracker of arXiv 2603.11404 (Hu, Liang, Richter,
+ * Yip, "Real-time Rendering-based Surgical Instrument Tracking via
+ * Evolutionary Optimization").
+ *
+ * The hot path is the fitness of a whole CMA-ES population (Sec. III-A.1,
+ * Sec. III-A.2): for every candidate state Theta = (T_r^c, q) the library
+ * runs the kinematics of the instrument links, projects the link meshes
+ * through a pinhole camera, rasterises a binary silhouette S and reduces it
+ * against the observed mask M to integer counts, all inside one kernel launch
+ * (no silhouette is written to memory).  Around it sit the device-resident
+ * CMA-ES update of Eq. (cmaes_update) and a per-frame tracking call.
+ *
+ * Conventions shared by every entry point
+ * - Status: every function returns trk_status; nothing throws across the ABI.
+ *   TRK_EINVAL means an argument was rejected before any device work was
+ *   queued.  TRK_ECUDA means a CUDA call failed (tracker_last_error() gives the
+ *   CUDA error string).
+ * - Streams: `stream` is a cudaStream_t passed as void*; NULL is the legacy
+ *   default stream.  Functions named *_host synchronise that stream before they
+ *   return; all others only enqueue work and return immediately.
+ * - Memory: pointers named *_dev are device pointers owned by the caller and
+ *   must stay valid until the queued work completes; pointers named *_host are
+ *   host pointers, read or written before the call returns.  The tracker owns
+ *   its copies of the mesh, chain and camera and its scratch buffers.
+ * - A state vector has d = 9 * n_instruments floats per candidate:
+ *   [r0 r1 r2 | x y z | qh1 qh2 qh3] per instrument (Sec. III-A.3): the
+ *   rotation (axis-angle vector, or look-at angles alpha, beta, gamma), the
+ *   translation in mm, and the unconstrained joint coordinates q-hat whose
+ *   inverse cosine map gives wrist pitch, wrist yaw and jaw angle.  Two
+ *   instruments are laid out [Theta_L, Theta_R] (Sec. III-B).
+ * - Masks: bit-packed rows, word w of row i holds pixels (i, 32w .. 32w+31),
+ *   bit b = pixel 32w+b; row stride ceil(W/32) words; bits past W are zero.
+ * - Pixel (i, j) samples the image point (u, v) = (j, i).  Vertices are
+ *   snapped to 1/256 px with round-half-even; a pixel is covered by a triangle
+ *   under integer edge functions with the top-left rule.
+ */
+#ifndef TRACKER_H
+#define TRACKER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TRK_OK = 0,
+    TRK_EINVAL = 1,   /* rejected argument (nothing was enqueued)                 */
+    TRK_ENOMEM = 2,   /* device or host allocation failed                          */
+    TRK_ECUDA = 3,    /* a CUDA runtime call failed                                */
+    TRK_EDEVICE = 4,  /* a kernel raised the device error word                     */
+    TRK_ETIMEOUT = 5, /* a bounded device wait expired                             */
+    TRK_EBUSY = 6     /* admission refused (not enough free memory or slots)       */
+} trk_status;
+
+#define TRK_MAX_FRAMES 16     /* kinematic frames per instrument                  */
+#define TRK_MAX_INSTRUMENTS 2 /* single arm or bi-manual (Sec. III-B)             */
+#define TRK_MAX_D 18          /* 9 * TRK_MAX_INSTRUMENTS                          */
+#define TRK_MAX_LAMBDA 1024   /* largest CMA-ES population                         */
+#define TRK_MAX_PIXELS (1280 * 1280) /* silhouette bitmap must fit one CTA's smem */
+
+enum { TRK_AXIS_NONE = 0, TRK_AXIS_X = 1, TRK_AXIS_Y = 2, TRK_AXIS_Z = 3 };
+enum { TRK_ROT_AXIS_ANGLE = 0, TRK_ROT_LOOKAT = 1 };
+enum { TRK_LOSS_XOR = 0, TRK_LOSS_ONE_MINUS_IOU = 1, TRK_LOSS_MSE_APP = 2 };
+
+/* One rigid link mesh in the coordinates of kinematic frame `frame`
+ * (the CAD vertices v_m of Sec. III-A.2).  Host arrays, copied at create. */
+typedef struct {
+    int32_t frame;         /* 0 .. n_frames-1                                  */
+    int32_t n_verts;
+    const float *verts;    /* [n_verts * 3], mm                                */
+    int32_t n_tris;
+    const int32_t *tris;   /* [n_tris * 3], indices into this mesh's verts     */
+} trk_link_mesh;
+
+/* Forward kinematics T_m^r(q) of one instrument (Sec. III-A.2), as a tree of
+ * frames below the end-effector frame E (the wrist-pitch frame, Sec. III-A):
+ *   T_f = T_parent(f) * Trans(offset_f) * Rot(axis_f, coef_f * q[joint_f]),
+ * parent -1 meaning E, parents listed before children.  q_i is recovered
+ * from the state's q-hat_i by the inverse cosine map with limits
+ * [q_lb_i, q_ub_i] (Sec. III-A.3).  The camera pose is T_r^c = [R | t]. */
+typedef struct {
+    int32_t n_frames;
+    int32_t parent[TRK_MAX_FRAMES];
+    double offset[TRK_MAX_FRAMES][3];
+    int32_t axis[TRK_MAX_FRAMES];
+    int32_t joint[TRK_MAX_FRAMES];  /* 0 .. 2                                */
+    double coef[TRK_MAX_FRAMES];
+    double q_lb[3], q_ub[3];
+    int32_t rot_param;     /* TRK_ROT_AXIS_ANGLE or TRK_ROT_LOOKAT               */
+    int32_t n_instruments; /* 1, or 2 for the bi-manual joint render            */
+} trk_chain;
+
+/* Pinhole intrinsics K (Sec. III-A.2).  256*cx and 256*cy must be integers. */
+typedef struct {
+    double fx, fy, cx, cy;
+    int32_t width, height;
+    double z_near;         /* mm; vertices closer are flagged                    */
+} trk_intrinsics;
+
+typedef struct {
+    int32_t loss_kind;     /* TRK_LOSS_*                                         */
+    float lambda_app;      /* appearance weight of Eq. render_loss (MSE_APP)     */
+    int32_t cull_backfaces;/* 0: union of all faces (default)                    */
+    int32_t lambda_max;    /* largest population eval_population will accept     */
+    int32_t cluster;       /* CTAs per candidate, 1..8 (0 = auto)                */
+    int32_t block_threads; /* threads per CTA: multiple of 32, >= 32 per instrument,
+                              <= 256 (0 = auto)                                  */
+} trk_config;
+
+typedef struct trk_tracker trk_tracker;
+typedef struct trk_cmaes trk_cmaes;
+
+/* Human-readable name of a status, and the last CUDA error text seen by this
+ * library on the calling thread (empty if none). */
+const char *trk_status_string(trk_status s);
+const char *tracker_last_error(void);
+
+/* Create a tracker on the current CUDA device: validates and copies the link
+ * meshes, the chain and the intrinsics to the device and allocates the
+ * per-candidate scratch (snapped vertices) for lambda_max candidates.
+ * Errors: TRK_EINVAL for out-of-range indices, frames, sizes, non-integer
+ * 256*cx, images larger than TRK_MAX_PIXELS; TRK_ENOMEM; TRK_ECUDA.
+ * Sec. III-A.2 (renderer inputs: v_m, T_m^r, K). */
+trk_status tracker_create(const trk_link_mesh *meshes, int32_t n_meshes, const trk_chain *chain,
+                          const trk_intrinsics *K, const trk_config *cfg, trk_tracker **out);
+trk_status tracker_destroy(trk_tracker *t);
+
+/* Sizes the tracker was created with (any pointer may be NULL). */
+trk_status tracker_info(const trk_tracker *t, int32_t *d, int32_t *n_verts, int32_t *n_tris,
+                        int32_t *width, int32_t *height, int32_t *words_per_row);
+
+/* Bit-pack an observed mask M_ref (Sec. III-A.2): mask_dev [H*W] bytes, nonzero
+ * = tool, into packed_dev [H*ceil(W/32)] words (layout above).  Asynchronous. */
+trk_status tracker_pack_mask(trk_tracker *t, const uint8_t *mask_dev, uint32_t *packed_dev, void *stream);
+
+/* THE HOT PATH.  Fitness of lam candidates (Sec. III-A.1-2):
+ *   params_dev [lam*d] FP32 states (layout above),
+ *   mask_packed_dev the packed observed mask,
+ *   loss_dev [lam] FP32 loss of the configured kind:
+ *     XOR            s + m - 2I          (MSE of binary images, Eq. render_loss)
+ *     ONE_MINUS_IOU  1 - I/(s + m - I)   (0 when the union is empty; Sec. IV-B metric)
+ *     MSE_APP        XOR + lambda_app |s - m|   (Eq. render_loss),
+ *   counts_dev [lam*4] int32 (s, I, m, culled) or NULL, with s = sum S,
+ *     I = sum S&M, m = sum M, culled = triangles skipped because a vertex was
+ *     behind z_near or outside the guard band (|u-cx|, |v-cy| > 2^14 px).
+ * One launch: kinematics, projection and 1/256 px snapping of every vertex,
+ * triangle setup and integer top-left rasterisation into a shared-memory
+ * bitmap per candidate, and the popcount reduction against the mask.
+ * lam = 0 is a no-op.  Errors: TRK_EINVAL if lam > lambda_max or a pointer is
+ * NULL; TRK_ECUDA on a launch failure.  Asynchronous on `stream`. */
+trk_status eval_population(trk_tracker *t, const float *params_dev, int32_t lam,
+                           const uint32_t *mask_packed_dev, float *loss_dev, int32_t *counts_dev,
+                           void *stream);
+
+/* Parity hook: the same launch as eval_population, additionally writing the
+ * snapped vertices snap_dev [lam*n_instruments*n_verts*2] int32 (1/256 px;
+ * INT32_MIN for a flagged vertex) and the unsnapped offsets from the principal
+ * point uv_dev [same shape] FP32 (u - cx, v - cy in px); either may be NULL. */
+trk_status eval_population_debug(trk_tracker *t, const float *params_dev, int32_t lam,
+                                 const uint32_t *mask_packed_dev, float *loss_dev, int32_t *counts_dev,
+                                 int32_t *snap_dev, float *uv_dev, void *stream);
+
+/* Render the union silhouette of one state into a packed bitmap
+ * (silhouette_dev [H*ceil(W/32)] words): used to make synthetic observations
+ * and for inspection, not by the fitness path.  Asynchronous. */
+trk_status tracker_render(trk_tracker *t, const float *params_dev, uint32_t *silhouette_dev, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Device-resident CMA-ES (Sec. III-A.1, Eq. cmaes_update; Sec. III-B block
+ * form).  The state (mean, sigma, C, its symmetric square root and inverse
+ * square root, the paths p_sigma and p_c, the generation counters and the
+ * best candidate) lives on the device in FP64; populations are FP32.
+ * Search coordinates are normalised: state = scales (.) x, C^(0) = I.
+ * Samples: x_k = m + sigma C^(1/2) z_k with z from Philox4x32-10 (counter
+ * (block, total generation, stream_id, 0), key = seed): 24-bit uniforms
+ * ((r >> 8) + 1/2) 2^-24 and the Box-Muller transform in FP32; the
+ * covariance, its eigendecomposition, the paths and the step size are FP64.
+ * Constants: Hansen's CMA-ES tutorial defaults for n = d, c_m = 1.
+ * ------------------------------------------------------------------------- */
+
+/* Create an optimiser for populations of lam (2..TRK_MAX_LAMBDA, <= the
+ * tracker's lambda_max) around mean_host [d] (physical units) with per-
+ * coordinate scales_host [d] and initial step sigma0 (normalised units).
+ * block_diag != 0 keeps C block-diagonal with 9x9 blocks (Sec. III-B).
+ * Synchronous (uploads the initial state). */
+trk_status cmaes_create(trk_tracker *t, int32_t lam, const double *mean_host, const double *scales_host,
+                        double sigma0, uint64_t seed, uint32_t stream_id, int32_t block_diag,
+                        trk_cmaes **out);
+trk_status cmaes_destroy(trk_cmaes *es);
+
+/* Restart the search around mean_dev [d] FP64 (physical units) on the device:
+ * C = I, sigma = sigma0, paths 0, frame-best cleared.  The total generation
+ * counter (the random-number stream position) keeps counting. */
+trk_status cmaes_reset_device(trk_cmaes *es, const double *mean_dev, void *stream);
+trk_status cmaes_reset_host(trk_cmaes *es, const double *mean_host, void *stream);
+
+/* Sample the next population into the optimiser's own buffer and, if
+ * params_dev is not NULL, copy it there ([lam*d] FP32).  Asynchronous. */
+trk_status cmaes_ask(trk_cmaes *es, float *params_dev, void *stream);
+
+/* The same as cmaes_ask with the standard normals supplied by the caller:
+ * z_dev [lam*d] FP64 replaces the Philox draw (for reproducing a sample or
+ * checking the update against another implementation).  Asynchronous. */
+trk_status cmaes_ask_normals(trk_cmaes *es, const double *z_dev, float *params_dev, void *stream);
+
+/* Copy the standard normals of the last population (z_dev [lam*d] FP64). */
+trk_status cmaes_last_normals(trk_cmaes *es, double *z_dev, void *stream);
+
+/* Update from loss_dev [lam] (lower is better; NaN ranks last) for the
+ * population of the last ask: stable ranking by (loss, index), weighted
+ * recombination, p_sigma, p_c, rank-one and rank-mu update of C, cumulative
+ * step-size adaptation, and an FP64 Jacobi eigendecomposition of C (warm-
+ * started from the previous eigenbasis) giving C^(1/2) and C^(-1/2).
+ * Asynchronous. */
+trk_status cmaes_tell(trk_cmaes *es, const float *loss_dev, void *stream);
+
+/* One generation in one launch: every candidate is sampled, evaluated against
+ * mask_packed_dev and the update is applied (the same arithmetic as
+ * cmaes_ask, eval_population and cmaes_tell in sequence). */
+trk_status cmaes_step(trk_cmaes *es, const uint32_t *mask_packed_dev, void *stream);
+
+/* Read the state (synchronises the stream).  Any output pointer may be NULL.
+ * mean/p_sigma/p_c [d] normalised, C [d*d], best_x [d] FP32 physical. */
+trk_status cmaes_get_state_host(trk_cmaes *es, double *mean, double *sigma, double *C, double *p_sigma,
+                                double *p_c, int32_t *gen, int32_t *gen_total, float *best_x,
+                                float *best_loss, void *stream);
+
+/* Device pointers of the optimiser's population and loss buffers. */
+trk_status cmaes_buffers(trk_cmaes *es, float **params_dev, float **loss_dev, float **best_x_dev);
+
+/* Per-frame tracking (Sec. III-A: the previous estimate seeds the next frame;
+ * joint readings, when given, replace the propagated joints).  Restarts the
+ * search around the current estimate (the previous frame's best, or the
+ * creation mean for the first frame), runs `generations` CMA-ES generations
+ * against the packed mask and makes the frame's best candidate the estimate.
+ * joint_reading_dev [3*n_instruments] FP32 measured joint angles q, or NULL.
+ * pose_out_dev [d] FP32 or NULL.  Asynchronous. */
+trk_status track_frame_device(trk_cmaes *es, const uint32_t *mask_packed_dev, int32_t generations,
+                              const float *joint_reading_dev, float *pose_out_dev, void *stream);
+
+/* The same from host memory: copies mask_host [H*W] bytes (pinned memory
+ * gives an asynchronous copy) and the optional joint_reading_host to the
+ * device, packs the mask, tracks, and copies the estimate back to
+ * pose_out_host [d] (and its loss to best_loss_out, if not NULL).
+ * Synchronises `stream` before returning. */
+trk_status track_frame_host(trk_cmaes *es, const uint8_t *mask_host, int32_t generations,
+                            const float *joint_reading_host, float *pose_out_host, float *best_loss_out,
+                            void *stream);
+
+/* Checkpoint: the whole optimiser state as a plain blob.  cmaes_save with
+ * blob = NULL sets *n to the size needed.  A loaded optimiser continues
+ * bit-identically.  Both synchronise the stream. */
+trk_status cmaes_save(trk_cmaes *es, void *blob, size_t *n, void *stream);
+trk_status cmaes_load(trk_cmaes *es, const void *blob, size_t n, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TRACKER_H */

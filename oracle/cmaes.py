@@ -93,10 +93,14 @@ class CMAES:
         self.best_loss = np.inf
         self.best_x = None
 
-    def ask(self):
-        """Sample lam candidates.  Returns FP32 physical params [lam, d]."""
-        z = philox.normals(self.seed, self.stream, self.gen_total, self.lam * self.d)
-        self.z = z.reshape(self.lam, self.d)
+    def normals(self):
+        """The standard normals of the next generation [lam, d]."""
+        return philox.normals(self.seed, self.stream, self.gen_total, self.lam * self.d).reshape(self.lam, self.d)
+
+    def ask(self, z=None):
+        """Sample lam candidates (from the given normals z [lam, d], else the
+        generator's).  Returns FP32 physical params [lam, d]."""
+        self.z = self.normals() if z is None else np.asarray(z, np.float64).reshape(self.lam, self.d)
         self.C_half = _sym_pow(self.C, 0.5, self.block)
         self.y = self.z @ self.C_half.T
         self.x = self.m[None, :] + self.sigma * self.y

@@ -12,7 +12,8 @@ Normal draws used by the CMA-ES sampler (the CUDA path implements the same
 generator independently): element n of a generation's lam x d block of
 standard normals comes from counter block b = n // 4,
 counter = (b, generation, stream, 0), key = (seed mod 2^32, seed >> 32); the
-four words r0..r3 give uniforms u = (r + 0.5) / 2^32 and Box-Muller pairs
+four words r0..r3 give 24-bit uniforms u = ((r >> 8) + 0.5) / 2^24 and
+Box-Muller pairs (evaluated here in FP64)
   z0 = sqrt(-2 ln u0) cos(2 pi u1), z1 = sqrt(-2 ln u0) sin(2 pi u1),
   z2 = sqrt(-2 ln u2) cos(2 pi u3), z3 = sqrt(-2 ln u2) sin(2 pi u3);
 element n takes z_(n mod 4).
@@ -53,8 +54,8 @@ def normals(seed: int, stream: int, generation: int, count: int) -> np.ndarray:
     ctr = np.stack([b, np.full(nb, generation, np.uint64), np.full(nb, stream, np.uint64),
                     np.zeros(nb, np.uint64)], axis=-1)
     key = np.broadcast_to(np.array([seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF], np.uint64), (nb, 2))
-    r = philox4x32_10(ctr, key).astype(np.float64)
-    u = (r + 0.5) / 4294967296.0
+    r = philox4x32_10(ctr, key)
+    u = ((r >> np.uint32(8)).astype(np.float64) + 0.5) / 16777216.0
     rad0 = np.sqrt(-2.0 * np.log(u[:, 0]))
     rad1 = np.sqrt(-2.0 * np.log(u[:, 2]))
     z = np.stack([rad0 * np.cos(2 * np.pi * u[:, 1]), rad0 * np.sin(2 * np.pi * u[:, 1]),

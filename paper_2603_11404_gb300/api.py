@@ -1,0 +1,259 @@
+"""Python face of the C ABI: the same entry points, taking torch CUDA tensors.
+
+Every function here only marshals arguments (pointers, sizes, the current
+torch stream) into the calls declared in include/tracker.h; all of the work
+runs in the library's CUDA kernels.  PyTorch supplies device memory and
+streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _abi
+from ._abi import call
+
+LOSS_XOR, LOSS_ONE_MINUS_IOU, LOSS_MSE_APP = 0, 1, 2
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        if not t.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(t.data_ptr())
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data_as(C.c_void_p)
+    raise TypeError(type(t))
+
+
+def _check_dev(t, dtype, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor")
+
+
+class Tracker:
+    """tracker_create(mesh, links, intrinsics) and the fitness entry points."""
+
+    def __init__(self, scene, loss_kind: int = LOSS_XOR, lambda_max: int = 64, cull_backfaces: bool = False,
+                 lambda_app: float = 0.0, cluster: int = 0, block_threads: int = 0):
+        self.scene = scene
+        K = scene.K
+        self._keep = []
+        meshes = (_abi.LinkMesh * len(scene.meshes))()
+        for i, m in enumerate(scene.meshes):
+            v = np.ascontiguousarray(m.verts, np.float32)
+            t = np.ascontiguousarray(m.tris, np.int32)
+            self._keep += [v, t]
+            meshes[i] = _abi.LinkMesh(int(m.frame), int(v.shape[0]), v.ctypes.data, int(t.shape[0]), t.ctypes.data)
+        ch = _abi.Chain()
+        ch.n_frames = len(scene.frames)
+        for f, fr in enumerate(scene.frames):
+            ch.parent[f] = fr.parent
+            for k in range(3):
+                ch.offset[f][k] = float(fr.offset[k])
+            ch.axis[f] = fr.axis
+            ch.joint[f] = fr.joint
+            ch.coef[f] = float(fr.coef)
+        for i in range(3):
+            ch.q_lb[i] = float(scene.q_lb[i])
+            ch.q_ub[i] = float(scene.q_ub[i])
+        ch.rot_param = int(scene.rot_param)
+        ch.n_instruments = int(scene.n_instruments)
+        Ki = _abi.Intrinsics(float(K.fx), float(K.fy), float(K.cx), float(K.cy), int(K.width), int(K.height),
+                             float(K.z_near))
+        cfg = _abi.Config(int(loss_kind), float(lambda_app), int(bool(cull_backfaces)), int(lambda_max),
+                          int(cluster), int(block_threads))
+        h = C.c_void_p()
+        call("tracker_create", meshes, len(scene.meshes), C.byref(ch), C.byref(Ki), C.byref(cfg), C.byref(h))
+        self.h = h
+        d, nv, nt, w, hh, wq = (C.c_int32() for _ in range(6))
+        call("tracker_info", h, C.byref(d), C.byref(nv), C.byref(nt), C.byref(w), C.byref(hh), C.byref(wq))
+        self.d, self.n_verts, self.n_tris = d.value, nv.value, nt.value
+        self.width, self.height, self.words_per_row = w.value, hh.value, wq.value
+        self.n_instruments = int(scene.n_instruments)
+        self.lambda_max = int(lambda_max)
+        self.loss_kind = int(loss_kind)
+
+    def close(self):
+        if getattr(self, "h", None):
+            call("tracker_destroy", self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- masks -------------------------------------------------------------
+    def pack_mask(self, mask: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """tracker_pack_mask: uint8 [H, W] (nonzero = tool) -> int32 [H, ceil(W/32)] packed rows."""
+        _check_dev(mask, torch.uint8, "mask")
+        if tuple(mask.shape) != (self.height, self.width):
+            raise ValueError("mask shape")
+        if out is None:
+            out = torch.empty((self.height, self.words_per_row), dtype=torch.int32, device=mask.device)
+        call("tracker_pack_mask", self.h, _ptr(mask), _ptr(out), _stream(stream))
+        return out
+
+    # -- fitness -----------------------------------------------------------
+    def eval_population(self, params: torch.Tensor, mask_packed: torch.Tensor, loss: torch.Tensor | None = None,
+                        counts: torch.Tensor | bool | None = None, stream=None):
+        """eval_population: params [lam, d] FP32 -> loss [lam] FP32 (and counts [lam, 4] int32:
+        s, I, m, culled when counts is True or a tensor)."""
+        _check_dev(params, torch.float32, "params")
+        _check_dev(mask_packed, torch.int32, "mask_packed")
+        lam = params.shape[0] if params.dim() == 2 else 0
+        if params.dim() != 2 or params.shape[1] != self.d:
+            raise ValueError("params must be [lam, d]")
+        if loss is None:
+            loss = torch.empty(lam, dtype=torch.float32, device=params.device)
+        if counts is True:
+            counts = torch.empty((lam, 4), dtype=torch.int32, device=params.device)
+        elif counts is False:
+            counts = None
+        call("eval_population", self.h, _ptr(params), lam, _ptr(mask_packed), _ptr(loss), _ptr(counts),
+             _stream(stream))
+        return (loss, counts) if counts is not None else loss
+
+    def eval_population_debug(self, params: torch.Tensor, mask_packed: torch.Tensor, stream=None):
+        """eval_population_debug: returns loss, counts [lam,4], snapped [lam, n_inst*V, 2] int32,
+        uv [lam, n_inst*V, 2] FP32 offsets from the principal point."""
+        _check_dev(params, torch.float32, "params")
+        lam = params.shape[0]
+        dev = params.device
+        loss = torch.empty(lam, dtype=torch.float32, device=dev)
+        counts = torch.empty((lam, 4), dtype=torch.int32, device=dev)
+        nv = self.n_instruments * self.n_verts
+        snap = torch.empty((lam, nv, 2), dtype=torch.int32, device=dev)
+        uv = torch.empty((lam, nv, 2), dtype=torch.float32, device=dev)
+        call("eval_population_debug", self.h, _ptr(params), lam, _ptr(mask_packed), _ptr(loss), _ptr(counts),
+             _ptr(snap), _ptr(uv), _stream(stream))
+        return loss, counts, snap, uv
+
+    def render(self, state: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """tracker_render: one state [d] -> packed silhouette int32 [H, ceil(W/32)]."""
+        _check_dev(state, torch.float32, "state")
+        if out is None:
+            out = torch.empty((self.height, self.words_per_row), dtype=torch.int32, device=state.device)
+        call("tracker_render", self.h, _ptr(state.reshape(-1).contiguous()), _ptr(out), _stream(stream))
+        return out
+
+
+def unpack_mask(packed: torch.Tensor, width: int) -> torch.Tensor:
+    """Packed rows -> uint8 [H, W] (inverse of pack_mask, for inspection and tests)."""
+    H, Wq = packed.shape
+    bits = torch.arange(32, device=packed.device, dtype=torch.int32)
+    u = ((packed.unsqueeze(-1) >> bits) & 1).to(torch.uint8).reshape(H, Wq * 32)
+    return u[:, :width].contiguous()
+
+
+class CMAES:
+    """Device-resident CMA-ES: cmaes_create / ask / tell / step / track_frame."""
+
+    def __init__(self, tracker: Tracker, lam: int, mean, scales, sigma0: float = 1.0, seed: int = 0,
+                 stream_id: int = 0, block_diag: bool = False):
+        self.tracker = tracker
+        self.lam, self.d = int(lam), tracker.d
+        mean = np.ascontiguousarray(mean, np.float64)
+        scales = np.ascontiguousarray(scales, np.float64)
+        if mean.shape != (self.d,) or scales.shape != (self.d,):
+            raise ValueError("mean/scales must have d entries")
+        h = C.c_void_p()
+        call("cmaes_create", tracker.h, self.lam, _ptr(mean), _ptr(scales), float(sigma0), int(seed) & (2 ** 64 - 1),
+             int(stream_id), int(bool(block_diag)), C.byref(h))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            call("cmaes_destroy", self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self, mean, stream=None):
+        mean = np.ascontiguousarray(mean, np.float64)
+        call("cmaes_reset_host", self.h, _ptr(mean), _stream(stream))
+
+    def ask(self, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty((self.lam, self.d), dtype=torch.float32, device="cuda")
+        call("cmaes_ask", self.h, _ptr(out), _stream(stream))
+        return out
+
+    def ask_normals(self, z: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """cmaes_ask_normals: sample with caller-supplied standard normals z [lam, d] FP64."""
+        _check_dev(z, torch.float64, "z")
+        if out is None:
+            out = torch.empty((self.lam, self.d), dtype=torch.float32, device="cuda")
+        call("cmaes_ask_normals", self.h, _ptr(z), _ptr(out), _stream(stream))
+        return out
+
+    def last_normals(self, stream=None) -> torch.Tensor:
+        """cmaes_last_normals: the standard normals [lam, d] FP64 of the last population."""
+        out = torch.empty((self.lam, self.d), dtype=torch.float64, device="cuda")
+        call("cmaes_last_normals", self.h, _ptr(out), _stream(stream))
+        return out
+
+    def tell(self, loss: torch.Tensor, stream=None):
+        _check_dev(loss, torch.float32, "loss")
+        call("cmaes_tell", self.h, _ptr(loss), _stream(stream))
+
+    def step(self, mask_packed: torch.Tensor, stream=None):
+        call("cmaes_step", self.h, _ptr(mask_packed), _stream(stream))
+
+    def state(self, stream=None) -> dict:
+        d = self.d
+        m = np.zeros(d); ps = np.zeros(d); pc = np.zeros(d); Cm = np.zeros(d * d)
+        sig = C.c_double(); g = C.c_int32(); gt = C.c_int32()
+        bx = np.zeros(d, np.float32); bl = C.c_float()
+        call("cmaes_get_state_host", self.h, _ptr(m), C.byref(sig), _ptr(Cm), _ptr(ps), _ptr(pc), C.byref(g),
+             C.byref(gt), _ptr(bx), C.byref(bl), _stream(stream))
+        return dict(m=m, sigma=sig.value, C=Cm.reshape(d, d), p_sigma=ps, p_c=pc, gen=g.value, gen_total=gt.value,
+                    best_x=bx, best_loss=bl.value)
+
+    def track_frame(self, mask_packed: torch.Tensor, generations: int, joint_reading: torch.Tensor | None = None,
+                    pose_out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """track_frame_device: asynchronous; returns pose_out [d] FP32 on the device."""
+        if pose_out is None:
+            pose_out = torch.empty(self.d, dtype=torch.float32, device="cuda")
+        call("track_frame_device", self.h, _ptr(mask_packed), int(generations), _ptr(joint_reading), _ptr(pose_out),
+             _stream(stream))
+        return pose_out
+
+    def track_frame_host(self, mask_u8, generations: int, joint_reading=None, stream=None):
+        """track_frame_host: host mask [H, W] uint8 (numpy or pinned tensor) -> (pose [d], best loss)."""
+        if isinstance(mask_u8, torch.Tensor):
+            assert not mask_u8.is_cuda and mask_u8.dtype == torch.uint8 and mask_u8.is_contiguous()
+        else:
+            mask_u8 = np.ascontiguousarray(mask_u8, np.uint8)
+        pose = np.zeros(self.d, np.float32)
+        bl = C.c_float()
+        jr = None if joint_reading is None else np.ascontiguousarray(joint_reading, np.float32)
+        call("track_frame_host", self.h, _ptr(mask_u8), int(generations), _ptr(jr), _ptr(pose), C.byref(bl),
+             _stream(stream))
+        return pose, bl.value
+
+    def save(self, stream=None) -> bytes:
+        n = C.c_size_t()
+        call("cmaes_save", self.h, None, C.byref(n), _stream(stream))
+        buf = (C.c_char * n.value)()
+        call("cmaes_save", self.h, buf, C.byref(n), _stream(stream))
+        return bytes(buf)
+
+    def load(self, blob: bytes, stream=None):
+        buf = (C.c_char * len(blob)).from_buffer_copy(blob)
+        call("cmaes_load", self.h, buf, len(blob), _stream(stream))

@@ -1,0 +1,94 @@
+// Stand-alone device-resident CMA-ES kernels (arXiv 2603.11404, Sec. III-A.1,
+// Eq. cmaes_update; block-diagonal covariance of Sec. III-B): reset, sample
+// (ask), update (tell) and the frame epilogue.  The arithmetic lives in
+// cma_device.cuh and is shared with the fused per-generation fitness kernel.
+#include "cma_device.cuh"
+
+namespace trk {
+
+__global__ void k_cma_reset(const CmaConst *__restrict__ kp, CmaState *st, const double *mean_dev, int from_est,
+                            const float *joint_reading, int n_inst)
+{
+    const CmaConst &k = *kp;
+    const int d = k.d, tid = threadIdx.x;
+    for (int i = tid; i < d; i += blockDim.x) {
+        double mi = from_est ? st->est[i] : mean_dev[i];
+        int b = i / 9, r = i - 9 * b;
+        if (joint_reading && r >= 6 && b < n_inst)
+            mi = qhat_from_q((double)joint_reading[3 * b + (r - 6)], k.q_lb[r - 6], k.q_ub[r - 6]);
+        st->est[i] = mi;
+        st->m[i] = mi / k.scales[i];
+        st->m_df[i] = split_df(st->m[i]);
+        st->p_sigma[i] = 0.0;
+        st->p_c[i] = 0.0;
+        st->ev[i] = 1.0;
+        st->best_x[i] = 0.0f;
+    }
+    for (int e = tid; e < d * d; e += blockDim.x) {
+        double v = (e / d == e % d) ? 1.0 : 0.0;
+        st->C[e] = v;
+        st->B[e] = v;
+        st->C_half[e] = v;
+        st->C_half_df[e] = make_float2((float)v, 0.0f);
+        st->C_inv_half[e] = v;
+    }
+    if (tid == 0) {
+        st->sigma = k.sigma0;
+        st->sigma_df = split_df(k.sigma0);
+        st->cs_pow = 1.0;
+        st->gen = 0;
+        st->best_loss = INFINITY;
+        st->jacobi_sweeps = 0;
+        st->warn = 0;
+    }
+}
+
+__global__ void k_cma_ask(const CmaConst *__restrict__ kp, CmaState *st, double *y, double *z_keep,
+                          float *params, const double *z_in)
+{
+    __shared__ float2 zs[kMaxD];
+    cma_sample_warp(*kp, st, blockIdx.x, z_in, y, z_keep, params, nullptr, zs, threadIdx.x);
+}
+
+constexpr int kTellThreads = 128;  // 4 warps: one per SM sub-partition's FP64 pipe
+
+__global__ void __launch_bounds__(kTellThreads) k_cma_tell(const CmaConst *__restrict__ kp, CmaState *st,
+                                                           const double *y, const float *params, const float *loss)
+{
+    __shared__ TellSmem S;
+    cma_tell_block(*kp, st, y, params, loss, S, threadIdx.x, blockDim.x);
+}
+
+__global__ void k_cma_finish(const CmaConst *__restrict__ kp, CmaState *st, float *pose_out)
+{
+    cma_finish_frame(*kp, st, pose_out, threadIdx.x, blockDim.x);
+}
+
+cudaError_t launch_cma_reset(const CmaConst *k, CmaState *st, const double *mean_dev, bool from_est,
+                             const float *joint_reading_dev, int n_inst, cudaStream_t s)
+{
+    k_cma_reset<<<1, 128, 0, s>>>(k, st, mean_dev, from_est ? 1 : 0, joint_reading_dev, n_inst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cma_ask(const CmaConst *k, int lam, CmaState *st, double *y, double *z_keep, float *params,
+                           const double *z_in, cudaStream_t s)
+{
+    k_cma_ask<<<lam, 32, 0, s>>>(k, st, y, z_keep, params, z_in);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cma_tell(const CmaConst *k, CmaState *st, const double *y, const float *params,
+                            const float *loss, cudaStream_t s)
+{
+    k_cma_tell<<<1, kTellThreads, 0, s>>>(k, st, y, params, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cma_finish_frame(const CmaConst *k, CmaState *st, float *pose_out, cudaStream_t s)
+{
+    k_cma_finish<<<1, 32, 0, s>>>(k, st, pose_out);
+    return cudaGetLastError();
+}
+
+}  // namespace trk

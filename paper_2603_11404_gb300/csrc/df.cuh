@@ -1,0 +1,156 @@
+// Double-float ("float-float") arithmetic on the FP32 pipes.
+//
+// A value is an unevaluated sum hi + lo of two floats with |lo| <= ulp(hi)/2,
+// about 48 significant bits.  The building blocks are the error-free
+// transformations TwoSum (Knuth, TAOCP vol. 2, 4.2.2) and FMA-based TwoProd
+// (Dekker 1971 / Ogita-Rump-Oishi 2005); add, multiply, divide and square root
+// follow Dekker's double-length algorithms.  Explicit _rn intrinsics keep the
+// compiler from contracting the transformations.  GB300 runs FP32 FMA at 128
+// lanes/clk/SM against ~1.6 FP64 FMA/clk/SM, so this is how the library gets
+// near-FP64 accuracy for the per-candidate kinematics.
+//
+// sin/cos: Cody-Waite reduction by pi/2 split into three floats (the first
+// with few bits, so n * P1 is exact), then the Taylor series of sin and cos on
+// [-pi/4, pi/4] to the 17th / 18th power, evaluated by Horner's rule.
+#pragma once
+
+#include <math.h>
+
+namespace trk {
+
+struct dfl {
+    float hi, lo;
+};
+
+__device__ __forceinline__ dfl df_from(float a) { return {a, 0.0f}; }
+
+__device__ __forceinline__ dfl quick_two_sum(float a, float b)  // |a| >= |b|
+{
+    float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ dfl two_sum_df(float a, float b)
+{
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+
+__device__ __forceinline__ dfl two_prod_df(float a, float b)
+{
+    float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+
+__device__ __forceinline__ dfl df_add(dfl a, dfl b)
+{
+    dfl s = two_sum_df(a.hi, b.hi);
+    dfl t = two_sum_df(a.lo, b.lo);
+    float e = __fadd_rn(s.lo, t.hi);
+    dfl u = quick_two_sum(s.hi, e);
+    return quick_two_sum(u.hi, __fadd_rn(u.lo, t.lo));
+}
+
+__device__ __forceinline__ dfl df_neg(dfl a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ dfl df_sub(dfl a, dfl b) { return df_add(a, df_neg(b)); }
+
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b)
+{
+    dfl p = two_prod_df(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.lo, p.lo);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return quick_two_sum(p.hi, e);
+}
+
+__device__ __forceinline__ dfl df_mul_f(dfl a, float b)
+{
+    dfl p = two_prod_df(a.hi, b);
+    return quick_two_sum(p.hi, __fmaf_rn(a.lo, b, p.lo));
+}
+
+// a * b + c
+__device__ __forceinline__ dfl df_fma(dfl a, dfl b, dfl c) { return df_add(df_mul(a, b), c); }
+
+__device__ __forceinline__ dfl df_div(dfl a, dfl b)
+{
+    float q1 = __fdiv_rn(a.hi, b.hi);
+    dfl r = df_sub(a, df_mul_f(b, q1));
+    float q2 = __fdiv_rn(r.hi, b.hi);
+    r = df_sub(r, df_mul_f(b, q2));
+    float q3 = __fdiv_rn(r.hi, b.hi);
+    return df_add(quick_two_sum(q1, q2), df_from(q3));
+}
+
+__device__ __forceinline__ dfl df_sqrt(dfl a)
+{
+    if (!(a.hi > 0.0f)) return {0.0f, 0.0f};
+    float s = __fsqrt_rn(a.hi);
+    dfl e = df_sub(a, two_prod_df(s, s));
+    return quick_two_sum(s, __fdiv_rn(e.hi, __fmul_rn(2.0f, s)));
+}
+
+// hi/lo split of a double done by the compiler (constant expressions only).
+#define DFL_CONST(x) dfl{(float)(x), (float)((x) - (double)(float)(x))}
+
+// 1/k! for k = 0..18 as double-float constants.
+__device__ __forceinline__ dfl inv_fact(int k)
+{
+    switch (k) {
+    case 2: return DFL_CONST(1.0 / 2.0);
+    case 3: return DFL_CONST(1.0 / 6.0);
+    case 4: return DFL_CONST(1.0 / 24.0);
+    case 5: return DFL_CONST(1.0 / 120.0);
+    case 6: return DFL_CONST(1.0 / 720.0);
+    case 7: return DFL_CONST(1.0 / 5040.0);
+    case 8: return DFL_CONST(1.0 / 40320.0);
+    case 9: return DFL_CONST(1.0 / 362880.0);
+    case 10: return DFL_CONST(1.0 / 3628800.0);
+    case 11: return DFL_CONST(1.0 / 39916800.0);
+    case 12: return DFL_CONST(1.0 / 479001600.0);
+    case 13: return DFL_CONST(1.0 / 6227020800.0);
+    case 14: return DFL_CONST(1.0 / 87178291200.0);
+    case 15: return DFL_CONST(1.0 / 1307674368000.0);
+    case 16: return DFL_CONST(1.0 / 20922789888000.0);
+    case 17: return DFL_CONST(1.0 / 355687428096000.0);
+    case 18: return DFL_CONST(1.0 / 6402373705728000.0);
+    default: return DFL_CONST(1.0);  // 0! and 1!
+    }
+}
+
+// sin and cos of a double-float angle (|x| up to ~1e4 keeps the reduction exact).
+__device__ __forceinline__ void df_sincos(dfl x, dfl &s, dfl &c)
+{
+    // pi/2 = P1 + P2 + P3; P1 = 201/128 has 8 significant bits
+    const float P1 = 1.5703125f;
+    const dfl P2 = DFL_CONST(1.5707963267948966 - 1.5703125);
+    const float n = rintf(__fmul_rn(x.hi, 0.636619772f));
+    dfl r = df_sub(x, df_from(__fmul_rn(n, P1)));  // n * P1 exact for |n| < 2^15
+    r = df_sub(r, df_mul_f(P2, n));
+    const dfl u = df_mul(r, r);
+    // sin r = r * sum_{j=0..8} (-1)^j u^j / (2j+1)!,  cos r = sum_{j=0..9} (-1)^j u^j / (2j)!
+    dfl ps = inv_fact(17);
+#pragma unroll
+    for (int j = 7; j >= 0; --j) {
+        dfl cj = inv_fact(2 * j + 1);
+        ps = df_fma(ps, u, (j & 1) ? df_neg(cj) : cj);
+    }
+    dfl pc = df_neg(inv_fact(18));
+#pragma unroll
+    for (int j = 8; j >= 0; --j) {
+        dfl cj = inv_fact(2 * j);
+        pc = df_fma(pc, u, (j & 1) ? df_neg(cj) : cj);
+    }
+    dfl sr = df_mul(ps, r);
+    dfl cr = pc;
+    int q = ((int)n) & 3;
+    dfl ss = (q & 1) ? cr : sr, cc = (q & 1) ? sr : cr;
+    if (q == 1 || q == 2) cc = df_neg(cc);  // cos: +c, -s, -c, +s
+    if (q >= 2) ss = df_neg(ss);            // sin: +s, +c, -s, -c
+    s = ss;
+    c = cc;
+}
+
+__device__ __forceinline__ double df_to_double(dfl a) { return (double)a.hi + (double)a.lo; }
+
+}  // namespace trk

@@ -1,0 +1,131 @@
+// Internal declarations shared by the CUDA translation units of the tracker
+// library (kernels in raster.cu and cmaes.cu, the C ABI in abi.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <math.h>
+
+#include "../../include/tracker.h"
+
+namespace trk {
+
+constexpr int kMaxFrames = TRK_MAX_FRAMES;
+constexpr int kMaxD = TRK_MAX_D;
+constexpr int kSnapFlag = INT32_MIN;          // snapped x of a flagged vertex
+constexpr int kBigListCap = 1024;              // large triangles deferred per CTA
+constexpr double kGuardPx = 16384.0;           // |u - cx|, |v - cy| limit (2^14 px)
+
+// Kinematic chain of one instrument in device-friendly form (Sec. III-A.2).
+// Constants also carry double-float (hi, lo) copies, split on the host, for the
+// per-candidate kinematics that run on the FP32 pipes.
+struct ChainDev {
+    int n_frames, n_inst, rot_param, pad;
+    int parent[kMaxFrames], axis[kMaxFrames], joint[kMaxFrames];
+    double offset[kMaxFrames][3];
+    double coef[kMaxFrames];
+    double q_lb[3], q_ub[3];
+    float2 offset_df[kMaxFrames][3];
+    float2 coef_df[kMaxFrames];
+    float2 lb_df[3], half_range_df[3], pi_over_range_df[3];  // lb, (ub-lb)/2, pi/(ub-lb)
+};
+
+// Pinhole camera (Sec. III-A.2) and image geometry.
+struct CamDev {
+    double fx, fy, z_near, guard;
+    int W, H, Wq, cx256, cy256;
+    float2 fx_df, fy_df;
+};
+
+// Everything one fitness launch needs.
+struct EvalArgs {
+    ChainDev ch;
+    CamDev cam;
+    const float4 *verts;   // [V] x, y, z, frame index (exact small float)
+    const int4 *tris;      // [T] i0, i1, i2, 0
+    int V, T;
+    const float *params;   // [lam * d]
+    int d, lam;
+    const uint32_t *mask;  // packed [H * Wq]
+    int2 *snap;            // scratch [lam * n_inst * V]
+    float *loss;           // [lam] or null
+    int *counts;           // [lam * 4] or null
+    int2 *snap_dbg;        // optional export of snapped vertices
+    float2 *uv_dbg;        // optional export of unsnapped offsets
+    uint32_t *silhouette;  // optional: write the union bitmap (render mode, lam == 1)
+    int loss_kind;
+    float lambda_app;
+    int cull;
+    // fused CMA-ES generation (all NULL for a plain fitness launch): every
+    // cluster samples its own candidate, the last CTA to finish runs the update
+    const struct CmaConst *cma_k;
+    struct CmaState *cma_st;
+    double *cma_y, *cma_z;     // [lam * d] steps and normals of the population
+    unsigned *cma_done;        // CTA ticket counter, zero between launches
+    float *cma_pose_out;       // frame estimate output (finish only), may be NULL
+    int cma_finish;            // 1: also make the frame's best the estimate
+};
+
+struct LaunchCfg {
+    int cluster;           // CTAs per candidate
+    int threads;           // threads per CTA
+    size_t smem;           // dynamic shared memory per CTA
+};
+
+// CMA-ES constants, host-computed in FP64 (Hansen's tutorial defaults).
+struct CmaConst {
+    int d, lam, mu, block;
+    double w[TRK_MAX_LAMBDA / 2];
+    double mu_eff, c_sigma, d_sigma, c_c, c_1, c_mu, c_m, chi_n, sigma0;
+    // derived on the host: sqrt(c_s (2 - c_s) mu_eff), sqrt(c_c (2 - c_c) mu_eff),
+    // ((1.4 + 2/(n+1)) chi_n)^2, c_s / d_s, 1 / chi_n
+    double ps_coef, pc_coef, hs_thr2, cs_over_ds, inv_chi;
+    double scales[kMaxD];
+    float2 scales_df[kMaxD];
+    double q_lb[3], q_ub[3];
+    unsigned long long seed;
+    unsigned stream_id;
+};
+
+// Device-resident CMA-ES state (FP64 except the FP32 population and best).
+struct CmaState {
+    double m[kMaxD], p_sigma[kMaxD], p_c[kMaxD];
+    double C[kMaxD * kMaxD], B[kMaxD * kMaxD], ev[kMaxD];
+    double C_half[kMaxD * kMaxD], C_inv_half[kMaxD * kMaxD];
+    double est[kMaxD];     // current estimate (physical units), seeds the next frame
+    double sigma;
+    double cs_pow;         // (1 - c_sigma)^(2 gen), for the h_sigma test
+    int gen, gen_total;
+    int jacobi_sweeps, warn;
+    float best_loss;       // best of the current frame (since the last reset)
+    float best_x[kMaxD];
+    // double-float copies for the sampler (FP32 pipes): C^(1/2), mean, sigma
+    float2 C_half_df[kMaxD * kMaxD];
+    float2 m_df[kMaxD];
+    float2 sigma_df;
+};
+
+// hi/lo split of a double into a double-float pair (host or device).
+__host__ __device__ inline float2 split_df(double x)
+{
+    float hi = (float)x;
+    return make_float2(hi, (float)(x - (double)hi));
+}
+
+cudaError_t launch_eval(const EvalArgs &a, const LaunchCfg &cfg, cudaStream_t s);
+size_t tell_smem_bytes();
+cudaError_t launch_pack_mask(const uint8_t *mask, uint32_t *packed, int W, int H, int Wq, cudaStream_t s);
+size_t eval_smem_bytes(const EvalArgs &a);
+cudaError_t prepare_eval(size_t smem);
+int eval_max_threads();
+
+cudaError_t launch_cma_reset(const CmaConst *k, CmaState *st, const double *mean_dev, bool from_est,
+                             const float *joint_reading_dev, int n_inst, cudaStream_t s);
+cudaError_t launch_cma_ask(const CmaConst *k, int lam, CmaState *st, double *y, double *z_keep, float *params,
+                           const double *z_in, cudaStream_t s);
+cudaError_t launch_cma_tell(const CmaConst *k, CmaState *st, const double *y, const float *params,
+                            const float *loss, cudaStream_t s);
+cudaError_t launch_cma_finish_frame(const CmaConst *k, CmaState *st, float *pose_out, cudaStream_t s);
+
+}  // namespace trk

@@ -1,0 +1,676 @@
+// Fitness of a CMA-ES population in one launch (arXiv 2603.11404, Sec. III-A.2):
+//   S = R(K(Pi(T_r^c T_m^r(q) v_m))),  counts (s, I, m) of S against M_ref,
+//   loss of Eq. render_loss / the 1 - IoU mask error of Sec. IV-B.
+//
+// Launch shape: one thread-block cluster of `cluster` CTAs per candidate.
+//   prologue CTA 0 of the cluster (in the fused CMA-ES mode) samples the
+//            candidate and composes its link transforms in double-float
+//            arithmetic; the other CTAs copy them through distributed shared
+//            memory.
+//   phase 1  every CTA projects its share of the vertices in compensated FP32
+//            (double-float, error-free TwoSum/TwoProd), snapping them to 1/256 px
+//            with round-half-even; the snapped vertices go to an L2-resident
+//            scratch array.
+//   phase 2  after a cluster barrier every CTA takes its share of the
+//            triangles: integer setup (orientation, top-left bias, bbox), then
+//            small triangles are rasterised by one thread each with int32
+//            incremental edge functions, larger ones by a whole warp with
+//            int64 edge functions and __ballot_sync coverage words.  Coverage
+//            is OR-ed into the CTA's own full-image bitmap in shared memory.
+//   phase 3  after a second cluster barrier CTA r ORs band r of all the
+//            cluster's bitmaps through distributed shared memory, ANDs with
+//            the observed mask, popcounts, and the cluster's counts meet in
+//            CTA 0, which writes counts and loss.
+// No silhouette image is written to global memory.
+#include <cooperative_groups.h>
+
+#include "cma_device.cuh"
+#include "df.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace trk {
+
+// ----------------------------------------------------------------------------
+// Per-candidate kinematics in double-float arithmetic (Sec. III-A.2, III-A.3)
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ dfl dfc(float2 v) { return {v.x, v.y}; }
+
+__device__ __forceinline__ dfl dot3(dfl a0, dfl b0, dfl a1, dfl b1, dfl a2, dfl b2)
+{
+    return df_add(df_add(df_mul(a0, b0), df_mul(a1, b1)), df_mul(a2, b2));
+}
+
+// Elementary rotation about x, y or z (identity for TRK_AXIS_NONE).
+__device__ __forceinline__ void rot_elem_df(int axis, dfl a, dfl R[9])
+{
+    const dfl one = df_from(1.0f), zero = df_from(0.0f);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) R[i] = (i % 4 == 0) ? one : zero;
+    if (axis == TRK_AXIS_NONE) return;
+    dfl s, c;
+    df_sincos(a, s, c);
+    if (axis == TRK_AXIS_X) { R[4] = c; R[5] = df_neg(s); R[7] = s; R[8] = c; }
+    if (axis == TRK_AXIS_Y) { R[0] = c; R[2] = s; R[6] = df_neg(s); R[8] = c; }
+    if (axis == TRK_AXIS_Z) { R[0] = c; R[1] = df_neg(s); R[3] = s; R[4] = c; }
+}
+
+__device__ __forceinline__ void mul3_df(const dfl A[9], const dfl B[9], dfl C[9])
+{
+    dfl T[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) T[3 * i + j] = dot3(A[3 * i], B[j], A[3 * i + 1], B[3 + j], A[3 * i + 2], B[6 + j]);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) C[i] = T[i];
+}
+
+// Pose rotation of T_r^c: axis-angle, R = cos(t) I + sin(t) [k]x + (1 - cos(t)) k k^T
+// with t = |r|, k = r / t (I + [r]x when t < 1e-8); or look-at Ry(gamma) Rx(alpha) Rz(beta).
+__device__ void pose_rotation_df(int rot_param, const float *r, dfl R[9])
+{
+    if (rot_param == TRK_ROT_LOOKAT) {
+        dfl Ry[9], Rx[9], Rz[9], T[9];
+        rot_elem_df(TRK_AXIS_Y, df_from(r[2]), Ry);
+        rot_elem_df(TRK_AXIS_X, df_from(r[0]), Rx);
+        rot_elem_df(TRK_AXIS_Z, df_from(r[1]), Rz);
+        mul3_df(Ry, Rx, T);
+        mul3_df(T, Rz, R);
+        return;
+    }
+    dfl r0 = df_from(r[0]), r1 = df_from(r[1]), r2 = df_from(r[2]);
+    dfl t = df_sqrt(dot3(r0, r0, r1, r1, r2, r2));
+    const dfl one = df_from(1.0f);
+    if (t.hi < 1e-8f) {
+        R[0] = one; R[1] = df_neg(r2); R[2] = r1;
+        R[3] = r2; R[4] = one; R[5] = df_neg(r0);
+        R[6] = df_neg(r1); R[7] = r0; R[8] = one;
+        return;
+    }
+    dfl k[3] = {df_div(r0, t), df_div(r1, t), df_div(r2, t)};
+    dfl s, c;
+    df_sincos(t, s, c);
+    dfl c1 = df_sub(one, c);
+    dfl Kx[9] = {df_from(0.f), df_neg(k[2]), k[1], k[2], df_from(0.f), df_neg(k[0]), df_neg(k[1]), k[0], df_from(0.f)};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            dfl v = df_fma(c1, df_mul(k[i], k[j]), df_mul(s, Kx[3 * i + j]));
+            R[3 * i + j] = (i == j) ? df_add(v, c) : v;
+        }
+}
+
+// Projective rows of every frame for one instrument state, computed by one
+// warp in double-float: rows (fx M0, fy M1, M2) of M = T_r^c T_f(q) with
+// T_f = T_parent * [Rot(axis_f, coef_f q_joint) | offset_f] and q from the
+// inverse cosine map q = lb + (ub-lb)/2 (1 - cos(pi (qh-lb)/(ub-lb))),
+// written as hi/lo float pairs (24 floats per frame).  Lanes work on
+// independent pieces (joint maps, pose rotation, joint rotations, matrix
+// entries).  scr: kComposeScratch float2.
+constexpr int kComposeScratch = 3 + 9 + kMaxFrames * 9 + kMaxFrames * 12;
+
+__device__ void compose_frames_warp(const ChainDev &ch, const CamDev &cam, const float *st, float *out,
+                                    float2 *scr, int lane)
+{
+    float2 *qs = scr, *Rs = scr + 3, *Js = scr + 12, *Ts = scr + 12 + kMaxFrames * 9;
+    const int nF = ch.n_frames;
+    if (lane < 3) {
+        dfl arg = df_mul(df_sub(df_from(st[6 + lane]), dfc(ch.lb_df[lane])), dfc(ch.pi_over_range_df[lane]));
+        dfl sn, cs;
+        df_sincos(arg, sn, cs);
+        dfl q = df_fma(dfc(ch.half_range_df[lane]), df_sub(df_from(1.0f), cs), dfc(ch.lb_df[lane]));
+        qs[lane] = make_float2(q.hi, q.lo);
+    }
+    if (lane == 3) {
+        dfl R[9];
+        pose_rotation_df(ch.rot_param, st, R);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) Rs[i] = make_float2(R[i].hi, R[i].lo);
+    }
+    __syncwarp();
+    if (lane < nF) {
+        dfl J[9];
+        rot_elem_df(ch.axis[lane], df_mul(dfc(ch.coef_df[lane]), dfc(qs[ch.joint[lane]])), J);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) Js[9 * lane + i] = make_float2(J[i].hi, J[i].lo);
+    }
+    __syncwarp();
+    for (int f = 0; f < nF; ++f) {  // parents first; lane = 4 i + j
+        if (lane < 12) {
+            int i = lane >> 2, jj = lane & 3;
+            const float2 *Jf = Js + 9 * f;
+            dfl L0 = jj < 3 ? dfc(Jf[jj]) : dfc(ch.offset_df[f][0]);
+            dfl L1 = jj < 3 ? dfc(Jf[3 + jj]) : dfc(ch.offset_df[f][1]);
+            dfl L2 = jj < 3 ? dfc(Jf[6 + jj]) : dfc(ch.offset_df[f][2]);
+            dfl v;
+            if (ch.parent[f] < 0) {
+                v = (i == 0) ? L0 : (i == 1 ? L1 : L2);
+            } else {
+                const float2 *P = Ts + 12 * ch.parent[f];
+                v = dot3(dfc(P[4 * i]), L0, dfc(P[4 * i + 1]), L1, dfc(P[4 * i + 2]), L2);
+                if (jj == 3) v = df_add(v, dfc(P[4 * i + 3]));
+            }
+            Ts[12 * f + lane] = make_float2(v.hi, v.lo);
+        }
+        __syncwarp();
+    }
+    for (int e = lane; e < nF * 12; e += 32) {  // M_f = [R | t] T_f, scaled rows
+        int f = e / 12, r = e - 12 * f, i = r >> 2, jj = r & 3;
+        const float2 *Tf = Ts + 12 * f;
+        dfl v = dot3(dfc(Rs[3 * i]), dfc(Tf[jj]), dfc(Rs[3 * i + 1]), dfc(Tf[4 + jj]), dfc(Rs[3 * i + 2]),
+                     dfc(Tf[8 + jj]));
+        if (jj == 3) v = df_add(v, df_from(st[3 + i]));
+        if (i == 0) v = df_mul(v, dfc(cam.fx_df));
+        if (i == 1) v = df_mul(v, dfc(cam.fy_df));
+        out[24 * f + r] = v.hi;
+        out[24 * f + 12 + r] = v.lo;
+    }
+    __syncwarp();
+}
+
+// ----------------------------------------------------------------------------
+// Compensated FP32 ("double-float") arithmetic: Knuth's TwoSum and the
+// FMA-based TwoProd give exact rounding errors; explicit _rn intrinsics keep
+// the compiler from contracting them.
+// ----------------------------------------------------------------------------
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e)
+{
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+// (hi + lo) . (x, y, z, 1)
+__device__ __forceinline__ DF df_affine(const float *h, const float *l, float x, float y, float z)
+{
+    float p0, e0, p1, e1, p2, e2, s, t0, t1, t2;
+    two_prod(h[0], x, p0, e0);
+    two_prod(h[1], y, p1, e1);
+    two_prod(h[2], z, p2, e2);
+    two_sum(p0, p1, s, t0);
+    two_sum(s, p2, s, t1);
+    two_sum(s, h[3], s, t2);
+    float err = __fadd_rn(__fadd_rn(t0, t1), __fadd_rn(t2, e0));
+    err = __fadd_rn(err, __fadd_rn(e1, e2));
+    err = __fadd_rn(err, __fmaf_rn(l[0], x, __fmaf_rn(l[1], y, __fmaf_rn(l[2], z, l[3]))));
+    DF r;
+    two_sum(s, err, r.hi, r.lo);
+    return r;
+}
+
+// a / b given rb = 1/b.hi (approximate): one correction step from the exact residual.
+__device__ __forceinline__ DF df_div(DF a, DF b, float rb)
+{
+    float q1 = __fmul_rn(a.hi, rb);
+    float p, e;
+    two_prod(q1, b.hi, p, e);
+    float r = __fsub_rn(__fsub_rn(a.hi, p), e);
+    r = __fadd_rn(r, __fsub_rn(a.lo, __fmul_rn(q1, b.lo)));
+    float q2 = __fmul_rn(r, rb);
+    DF o;
+    two_sum(q1, q2, o.hi, o.lo);
+    return o;
+}
+
+// Round-half-even of 256 (hi + lo), exact for |256 hi| < 2^22 (the guard band).
+__device__ __forceinline__ int snap256(DF u)
+{
+    float a = __fmul_rn(u.hi, 256.0f);
+    float b = __fmul_rn(u.lo, 256.0f);
+    float n = rintf(a);
+    float d = __fsub_rn(a, n);
+    if (d == 0.5f && b > 0.0f) n = __fadd_rn(n, 1.0f);
+    else if (d == -0.5f && b < 0.0f) n = __fsub_rn(n, 1.0f);
+    return (int)n;
+}
+
+// ----------------------------------------------------------------------------
+// Triangle setup shared by the raster paths.
+// ----------------------------------------------------------------------------
+struct TriSetup {
+    int x[3], y[3];       // snapped vertices, positive orientation
+    int j0, j1, i0, i1;   // pixel bbox clamped to the image
+    int spanx, spany;     // vertex bbox extent in 1/256 px
+};
+
+// Returns 0 = nothing to draw, 1 = draw, 2 = culled for a flagged vertex.
+// The clipped pixel bounding box is tested first: most triangles of a fine
+// mesh contain no pixel centre and leave before the orientation test.
+__device__ __forceinline__ int tri_setup(int2 a, int2 b, int2 c, int W, int H, int cull, TriSetup &t)
+{
+    if (a.x == kSnapFlag || b.x == kSnapFlag || c.x == kSnapFlag) return 2;
+    int xmn = min(a.x, min(b.x, c.x)), xmx = max(a.x, max(b.x, c.x));
+    int ymn = min(a.y, min(b.y, c.y)), ymx = max(a.y, max(b.y, c.y));
+    t.j0 = max(0, (xmn + 255) >> 8);   // ceil(x / 256)
+    t.j1 = min(W - 1, xmx >> 8);       // floor(x / 256)
+    t.i0 = max(0, (ymn + 255) >> 8);
+    t.i1 = min(H - 1, ymx >> 8);
+    if (t.j0 > t.j1 || t.i0 > t.i1) return 0;
+    t.spanx = xmx - xmn;
+    t.spany = ymx - ymn;
+    long long A;
+    if (t.spanx < (1 << 15) && t.spany < (1 << 15)) {  // |products| < 2^30: int32 is exact
+        A = (long long)((b.x - a.x) * (c.y - a.y) - (c.x - a.x) * (b.y - a.y));
+    } else {
+        A = (long long)(b.x - a.x) * (long long)(c.y - a.y) - (long long)(c.x - a.x) * (long long)(b.y - a.y);
+    }
+    if (A == 0) return 0;
+    if (cull && A > 0) return 0;
+    if (A < 0) {
+        int2 tmp = b;
+        b = c;
+        c = tmp;
+    }
+    t.x[0] = a.x; t.y[0] = a.y;
+    t.x[1] = b.x; t.y[1] = b.y;
+    t.x[2] = c.x; t.y[2] = c.y;
+    return 1;
+}
+
+// Edge k runs from vertex k to vertex k+1.  e_k(j, i) = dx (256 i - y_k)
+// - dy (256 j - x_k) - bias_k, bias 0 on top-left edges (dy < 0, or dy == 0 and
+// dx > 0) and 1 otherwise, so a pixel is covered iff every e_k >= 0.
+__device__ __forceinline__ long long edge64(const TriSetup &t, int k, long long Px, long long Py)
+{
+    int k1 = (k == 2) ? 0 : k + 1;
+    long long dx = t.x[k1] - t.x[k], dy = t.y[k1] - t.y[k];
+    int bias = (dy < 0 || (dy == 0 && dx > 0)) ? 0 : 1;
+    return dx * (Py - t.y[k]) - dy * (Px - t.x[k]) - bias;
+}
+
+// One thread, int32 incremental edges.  Requires spanx < 32 px and spany < 64 px
+// so that |e| < 2^28 over the bbox and a row fits one 64-bit word window.
+// Each row collects its coverage most-significant-bit first (bits = 2 bits +
+// sign), then one bit reversal puts pixel j0 at bit 0.
+__device__ __forceinline__ void raster_small(const TriSetup &t, uint32_t *bm, int Wq)
+{
+    int r[3], cs[3], rs[3];
+    long long Px = 256LL * t.j0, Py = 256LL * t.i0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        int k1 = (k == 2) ? 0 : k + 1;
+        int dx = t.x[k1] - t.x[k], dy = t.y[k1] - t.y[k];
+        r[k] = (int)edge64(t, k, Px, Py);
+        cs[k] = dy * 256;
+        rs[k] = dx * 256;
+    }
+    const int jb = t.j0 & ~31;
+    const int off = t.j0 - jb;
+    const int nb = t.j1 - t.j0 + 1;  // 1..32
+    uint32_t *row = bm + (size_t)t.i0 * Wq + (jb >> 5);
+    for (int i = t.i0; i <= t.i1; ++i) {
+        int a0 = r[0], a1 = r[1], a2 = r[2];
+        uint32_t bits = 0u;
+#pragma unroll 4
+        for (int n = 0; n < nb; ++n) {
+            bits = (bits << 1) | ((uint32_t)(~(a0 | a1 | a2)) >> 31);
+            a0 -= cs[0];
+            a1 -= cs[1];
+            a2 -= cs[2];
+        }
+        if (bits) {
+            unsigned long long m = (unsigned long long)(__brev(bits) >> (32 - nb)) << off;
+            uint32_t lo = (uint32_t)m, hi = (uint32_t)(m >> 32);
+            if (lo) atomicOr(row, lo);
+            if (hi) atomicOr(row + 1, hi);
+        }
+        r[0] += rs[0];
+        r[1] += rs[1];
+        r[2] += rs[2];
+        row += Wq;
+    }
+}
+
+// One whole warp per triangle: lane l tests pixel 32 w + l of word w, int64 edges.
+__device__ void raster_warp(const TriSetup &t, uint32_t *bm, int Wq, int lane)
+{
+    for (int i = t.i0; i <= t.i1; ++i) {
+        long long Py = 256LL * i;
+        for (int w = t.j0 >> 5; w <= (t.j1 >> 5); ++w) {
+            int j = (w << 5) + lane;
+            bool in = (j >= t.j0) && (j <= t.j1);
+            if (in) {
+                long long Px = 256LL * j;
+                long long e = edge64(t, 0, Px, Py) | edge64(t, 1, Px, Py) | edge64(t, 2, Px, Py);
+                in = e >= 0;
+            }
+            unsigned m = __ballot_sync(0xffffffffu, in);
+            if (lane == 0 && m) atomicOr(bm + (size_t)i * Wq + w, m);
+        }
+    }
+}
+
+// One thread, int64, any size (overflow of the deferred list).
+__device__ void raster_serial(const TriSetup &t, uint32_t *bm, int Wq)
+{
+    for (int i = t.i0; i <= t.i1; ++i)
+        for (int j = t.j0; j <= t.j1; ++j) {
+            long long Px = 256LL * j, Py = 256LL * i;
+            if ((edge64(t, 0, Px, Py) | edge64(t, 1, Px, Py) | edge64(t, 2, Px, Py)) >= 0)
+                atomicOr(bm + (size_t)i * Wq + (j >> 5), 1u << (j & 31));
+        }
+}
+
+// Camera-frame position of one vertex from its frame's projective rows (hi/lo
+// pairs), perspective division and snap: int2 (U, V) in 1/256 px, or the flag
+// value when the vertex is behind z_near or outside the guard band; uv gets
+// the unsnapped offsets from the principal point.
+__device__ __forceinline__ int2 project_vertex(float4 p, const float *Mh, const CamDev &cam, float2 &uv)
+{
+    DF X = df_affine(Mh + 0, Mh + 12, p.x, p.y, p.z);
+    DF Y = df_affine(Mh + 4, Mh + 16, p.x, p.y, p.z);
+    DF Z = df_affine(Mh + 8, Mh + 20, p.x, p.y, p.z);
+    int2 o = make_int2(kSnapFlag, kSnapFlag);
+    uv = make_float2(0.f, 0.f);
+    if (Z.hi >= (float)cam.z_near) {
+        float rz = __frcp_rn(Z.hi);
+        DF u = df_div(X, Z, rz), w = df_div(Y, Z, rz);
+        uv = make_float2(__fadd_rn(u.hi, u.lo), __fadd_rn(w.hi, w.lo));
+        const float guard = (float)cam.guard;
+        if (fabsf(u.hi) <= guard && fabsf(w.hi) <= guard)
+            o = make_int2(snap256(u) + cam.cx256, snap256(w) + cam.cy256);
+    }
+    return o;
+}
+
+// ----------------------------------------------------------------------------
+// The fused fitness kernel.
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(256, 4) k_eval(EvalArgs a)
+{
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int K = (int)cluster.num_blocks();
+    const int c = blockIdx.y;  // candidate
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+    const int nI = a.ch.n_inst, nF = a.ch.n_frames;
+    const int W = a.cam.W, H = a.cam.H, Wq = a.cam.Wq;
+    const int nwords = H * Wq;
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2 *scr = reinterpret_cast<float2 *>(smem);                           // [nI*kComposeScratch]
+    uint32_t *bm = reinterpret_cast<uint32_t *>(scr + nI * kComposeScratch);  // [H*Wq]
+    float *sM = reinterpret_cast<float *>(bm + ((nwords + 3) & ~3));          // [nI*nF*24]
+    int *big = reinterpret_cast<int *>(sM + nI * nF * 24);                    // [kBigListCap]
+    int *sacc = big + kBigListCap;                                            // [8]: s I m culled nbig
+    __shared__ int red[4][32];
+    __shared__ float s_par[kMaxD];
+    __shared__ float2 s_z[kMaxD];
+    __shared__ int s_last;
+
+    for (int w = tid; w < nwords; w += nthr) bm[w] = 0u;
+    if (tid < 8) sacc[tid] = 0;
+    // ---- prologue: CTA 0 of the cluster samples (fused CMA-ES mode) and
+    //      composes the candidate's frames in FP64; the others copy them ----
+    if (rank == 0) {
+        const float *par = a.params + (size_t)c * a.d;
+        if (a.cma_st) {
+            if (warp == 0)
+                cma_sample_warp(*a.cma_k, a.cma_st, c, nullptr, a.cma_y, a.cma_z, const_cast<float *>(a.params),
+                                s_par, s_z, lane);
+            __syncthreads();
+            par = s_par;
+        }
+        if (warp < nI)
+            compose_frames_warp(a.ch, a.cam, par + 9 * warp, sM + warp * nF * 24, scr + warp * kComposeScratch,
+                                lane);
+    }
+    cluster.sync();
+    if (rank != 0) {
+        const float *src = cluster.map_shared_rank(sM, 0);
+        for (int e = tid; e < nI * nF * 24; e += nthr) sM[e] = src[e];
+    }
+    __syncthreads();
+
+    // ---- phase 1: project and snap this CTA's share of the vertices, two in flight ----
+    const int gtid = rank * nthr + tid, gstride = K * nthr;
+    int2 *snapc = a.snap + (size_t)c * nI * a.V;
+    const int NV = nI * a.V;
+    for (int idx0 = gtid; idx0 < NV; idx0 += 2 * gstride) {
+        const int idx1 = idx0 + gstride;
+        const bool has1 = idx1 < NV;
+        int b0 = idx0 / a.V, b1 = has1 ? idx1 / a.V : b0;
+        float4 p0 = a.verts[idx0 - b0 * a.V];
+        float4 p1 = has1 ? a.verts[idx1 - b1 * a.V] : p0;
+        float2 uv0, uv1;
+        int2 o0 = project_vertex(p0, sM + (b0 * nF + (int)p0.w) * 24, a.cam, uv0);
+        int2 o1 = project_vertex(p1, sM + (b1 * nF + (int)p1.w) * 24, a.cam, uv1);
+        snapc[idx0] = o0;
+        if (a.snap_dbg) a.snap_dbg[(size_t)c * NV + idx0] = o0;
+        if (a.uv_dbg) a.uv_dbg[(size_t)c * NV + idx0] = uv0;
+        if (has1) {
+            snapc[idx1] = o1;
+            if (a.snap_dbg) a.snap_dbg[(size_t)c * NV + idx1] = o1;
+            if (a.uv_dbg) a.uv_dbg[(size_t)c * NV + idx1] = uv1;
+        }
+    }
+    __threadfence();
+    cluster.sync();
+
+    // ---- phase 2: triangles -> this CTA's bitmap, next triangle's loads in flight ----
+    int culled = 0;
+    const int NT = nI * a.T;
+    {
+        int tt = gtid;
+        int4 tri_c = make_int4(0, 0, 0, 0), tri_n = make_int4(0, 0, 0, 0);
+        int bc = 0, bn = 0;
+        int2 v0 = make_int2(0, 0), v1 = v0, v2 = v0;
+        if (tt < NT) {
+            bc = tt / a.T;
+            tri_c = a.tris[tt - bc * a.T];
+            const int2 *sv = snapc + bc * a.V;
+            // written by other CTAs of the cluster in phase 1: read through L2
+            v0 = __ldcg(sv + tri_c.x);
+            v1 = __ldcg(sv + tri_c.y);
+            v2 = __ldcg(sv + tri_c.z);
+        }
+        int tn = tt + gstride;
+        if (tn < NT) {
+            bn = tn / a.T;
+            tri_n = a.tris[tn - bn * a.T];
+        }
+        while (tt < NT) {
+            const int tnn = tn + gstride;
+            int2 w0 = make_int2(0, 0), w1 = w0, w2 = w0;
+            int4 tri_nn = make_int4(0, 0, 0, 0);
+            int bnn = 0;
+            if (tn < NT) {
+                const int2 *svn = snapc + bn * a.V;
+                w0 = __ldcg(svn + tri_n.x);
+                w1 = __ldcg(svn + tri_n.y);
+                w2 = __ldcg(svn + tri_n.z);
+            }
+            if (tnn < NT) {
+                bnn = tnn / a.T;
+                tri_nn = a.tris[tnn - bnn * a.T];
+            }
+            TriSetup t;
+            int st = tri_setup(v0, v1, v2, W, H, a.cull, t);
+            if (st == 2) ++culled;
+            if (st == 1) {
+                if (t.spanx < 32 * 256 && t.spany < 64 * 256) {
+                    raster_small(t, bm, Wq);
+                } else {
+                    int slot = atomicAdd(&sacc[4], 1);
+                    if (slot < kBigListCap) big[slot] = tt;
+                    else raster_serial(t, bm, Wq);
+                }
+            }
+            tt = tn;
+            tn = tnn;
+            v0 = w0;
+            v1 = w1;
+            v2 = w2;
+            tri_n = tri_nn;
+            bn = bnn;
+        }
+    }
+    __syncthreads();
+    const int nbig = min(sacc[4], kBigListCap);
+    for (int e = warp; e < nbig; e += nwarp) {
+        int tt = big[e];
+        int b = tt / a.T;
+        int4 tri = a.tris[tt - b * a.T];
+        const int2 *sv = snapc + b * a.V;
+        TriSetup t;
+        tri_setup(__ldcg(sv + tri.x), __ldcg(sv + tri.y), __ldcg(sv + tri.z), W, H, a.cull, t);
+        raster_warp(t, bm, Wq, lane);
+    }
+    cluster.sync();
+
+    // ---- phase 3: OR the cluster's bitmaps over this CTA's band, count ----
+    const int per = (nwords + K - 1) / K;
+    const int w0 = rank * per, w1 = min(nwords, w0 + per);
+    const uint32_t *rbm[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) rbm[q] = cluster.map_shared_rank(bm, q < K ? q : 0);
+    int s = 0, I = 0, m = 0;
+    for (int w = w0 + tid; w < w1; w += nthr) {
+        uint32_t part[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) part[q] = (q < K) ? rbm[q][w] : 0u;
+        uint32_t M = a.mask[w];
+        uint32_t S = 0u;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) S |= part[q];
+        s += __popc(S);
+        I += __popc(S & M);
+        m += __popc(M);
+        if (a.silhouette) a.silhouette[w] = S;
+    }
+    for (int o = 16; o; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        I += __shfl_xor_sync(0xffffffffu, I, o);
+        m += __shfl_xor_sync(0xffffffffu, m, o);
+        culled += __shfl_xor_sync(0xffffffffu, culled, o);
+    }
+    if (lane == 0) {
+        red[0][warp] = s;
+        red[1][warp] = I;
+        red[2][warp] = m;
+        red[3][warp] = culled;
+    }
+    __syncthreads();
+    if (tid < 4) {
+        int acc = 0;
+        for (int w = 0; w < nwarp; ++w) acc += red[tid][w];
+        atomicAdd(cluster.map_shared_rank(&sacc[tid], 0), acc);
+    }
+    cluster.sync();
+    if (rank == 0 && tid == 0) {
+        int S_ = sacc[0], I_ = sacc[1], M_ = sacc[2], C_ = sacc[3];
+        if (a.counts) {
+            a.counts[4 * c + 0] = S_;
+            a.counts[4 * c + 1] = I_;
+            a.counts[4 * c + 2] = M_;
+            a.counts[4 * c + 3] = C_;
+        }
+        if (a.loss) {
+            int x = S_ + M_ - 2 * I_;
+            float L;
+            if (a.loss_kind == TRK_LOSS_ONE_MINUS_IOU) {
+                int U = S_ + M_ - I_;
+                L = (U > 0) ? __fsub_rn(1.0f, __fdiv_rn((float)I_, (float)U)) : 0.0f;
+            } else if (a.loss_kind == TRK_LOSS_MSE_APP) {
+                L = __fadd_rn((float)x, __fmul_rn(a.lambda_app, (float)abs(S_ - M_)));
+            } else {
+                L = (float)x;
+            }
+            a.loss[c] = L;
+        }
+    }
+    if (a.cma_st) {  // the last CTA to finish updates the search distribution
+        if (tid == 0) {
+            __threadfence();
+            unsigned ticket = atomicAdd(a.cma_done, 1u);
+            s_last = (ticket == gridDim.x * gridDim.y - 1);
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            TellSmem &S = *reinterpret_cast<TellSmem *>(smem);  // the cluster no longer reads this CTA's smem
+            cma_tell_block(*a.cma_k, a.cma_st, a.cma_y, a.params, a.loss, S, tid, nthr);
+            __syncthreads();
+            if (a.cma_finish) cma_finish_frame(*a.cma_k, a.cma_st, a.cma_pose_out, tid, nthr);
+            if (tid == 0) *a.cma_done = 0u;
+        }
+    }
+}
+
+size_t tell_smem_bytes() { return sizeof(TellSmem); }
+
+size_t eval_smem_bytes(const EvalArgs &a)
+{
+    size_t nwords = (size_t)a.cam.H * a.cam.Wq;
+    return (size_t)a.ch.n_inst * kComposeScratch * sizeof(float2) + ((nwords + 3) & ~(size_t)3) * 4 +
+           (size_t)a.ch.n_inst * a.ch.n_frames * 24 * 4 + (size_t)kBigListCap * 4 + 8 * 4;
+}
+
+int eval_max_threads() { return 1024; }
+
+cudaError_t prepare_eval(size_t smem)
+{
+    // The attribute is per function: raise it to the largest size any tracker needs.
+    static size_t set_to = 0;
+    if (smem <= set_to) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) set_to = smem;
+    return e;
+}
+
+cudaError_t launch_eval(const EvalArgs &a, const LaunchCfg &cfg, cudaStream_t s)
+{
+    if (a.lam == 0) return cudaSuccess;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(cfg.cluster, a.lam, 1);
+    lc.blockDim = dim3(cfg.threads, 1, 1);
+    lc.dynamicSmemBytes = cfg.smem;
+    lc.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cfg.cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    return cudaLaunchKernelEx(&lc, k_eval, a);
+}
+
+// ----------------------------------------------------------------------------
+// Mask packing: one warp per 32-pixel word, coverage by __ballot_sync.
+// ----------------------------------------------------------------------------
+__global__ void k_pack_mask(const uint8_t *mask, uint32_t *packed, int W, int H, int Wq)
+{
+    long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (gw >= (long long)H * Wq) return;
+    int i = (int)(gw / Wq), w = (int)(gw - (long long)i * Wq);
+    int j = w * 32 + lane;
+    bool on = (j < W) && mask[(size_t)i * W + j] != 0;
+    unsigned b = __ballot_sync(0xffffffffu, on);
+    if (lane == 0) packed[gw] = b;
+}
+
+cudaError_t launch_pack_mask(const uint8_t *mask, uint32_t *packed, int W, int H, int Wq, cudaStream_t s)
+{
+    long long threads = (long long)H * Wq * 32;
+    int blocks = (int)((threads + 255) / 256);
+    if (blocks == 0) return cudaSuccess;
+    k_pack_mask<<<blocks, 256, 0, s>>>(mask, packed, W, H, Wq);
+    return cudaGetLastError();
+}
+
+}  // namespace trk

@@ -330,20 +330,27 @@ def corrupt_mask(mask: np.ndarray, rng: np.random.Generator, flip_p: float = 0.0
     n_tool = tool.shape[0]
     if n_tool > 0:
         target = rng.uniform(*occ_range)
-        ii, jj = np.mgrid[0:H, 0:W]
         occluded = np.zeros_like(m)
+        tool_mask = mask.astype(bool)
+        n_occ = 0
         scale = max(4.0, math.sqrt(n_tool) / 4)
         for _ in range(max_ellipses):
-            if (occluded & mask.astype(bool)).sum() >= target * n_tool:
+            if n_occ >= target * n_tool:
                 break
             ci, cj = tool[rng.integers(n_tool)]
             a, b = rng.uniform(0.3, 1.0, size=2) * scale
             th = rng.uniform(0, math.pi)
             c, s = math.cos(th), math.sin(th)
+            r = int(math.ceil(max(a, b))) + 1
+            i0, i1, j0, j1 = max(0, ci - r), min(H, ci + r + 1), max(0, cj - r), min(W, cj + r + 1)
+            ii, jj = np.mgrid[i0:i1, j0:j1]
             dx, dy = jj - cj, ii - ci
             u = (c * dx + s * dy) / a
             v = (-s * dx + c * dy) / b
-            occluded |= (u * u + v * v) <= 1.0
+            win = occluded[i0:i1, j0:j1]
+            before = int((win & tool_mask[i0:i1, j0:j1]).sum())
+            win |= (u * u + v * v) <= 1.0
+            n_occ += int((win & tool_mask[i0:i1, j0:j1]).sum()) - before
         m &= ~occluded
     flips = rng.random((H, W)) < flip_p
     return (m ^ flips).astype(np.uint8)

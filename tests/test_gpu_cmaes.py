@@ -1,0 +1,226 @@
+"""Parity of the device CMA-ES and tracker with the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle.cmaes import CMAES as OCMAES
+from oracle.tracker import track_frame as oracle_track_frame
+from paper_2603_11404_gb300 import workload as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_11404_gb300 import build
+    build.build()
+    from paper_2603_11404_gb300 import api as a
+    return a
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(1e-300, np.abs(b).max())
+
+
+def _quadratic_loss(P, target, wts):
+    return (((P.astype(np.float64) - target) ** 2) @ wts).astype(np.float32)
+
+
+@pytest.mark.parametrize("d,lam,block", [(9, 16, False), (9, 64, False), (18, 64, True), (18, 32, False)])
+def test_ask_tell_state_parity(api, d, lam, block):
+    n_inst = d // 9
+    sc = wl.make_scene("c1", "c1", n_instruments=n_inst)
+    tr = api.Tracker(sc, lambda_max=lam)
+    rng = np.random.default_rng(d * 100 + lam)
+    mean = rng.normal(size=d) * 0.1 + np.tile([0, 0, 0, 0, 0, 100, 0, 0, 0.4], n_inst)
+    scales = wl.default_scales(d)
+    g = api.CMAES(tr, lam, mean, scales, sigma0=0.8, seed=1234 + d, stream_id=3, block_diag=block)
+    o = OCMAES(d, lam, mean, scales, sigma0=0.8, seed=1234 + d, stream=3, block_diag=block)
+    target = mean + rng.normal(size=d) * scales * 3
+    wts = rng.uniform(0.5, 5.0, size=d) / scales ** 2
+    n_ulp_diff = 0
+    for gen in range(25):
+        z = o.normals()  # the same standard normals on both sides
+        Pg = g.ask_normals(torch.from_numpy(z).cuda()).cpu().numpy()
+        Po = o.ask(z)
+        dif = Pg != Po
+        if dif.any():
+            ulps = np.abs(Pg.view(np.int32)[dif].astype(np.int64) - Po.view(np.int32)[dif].astype(np.int64))
+            assert ulps.max() <= 1
+            n_ulp_diff += int(dif.sum())
+        loss = _quadratic_loss(Po, target, wts)
+        g.tell(torch.from_numpy(loss).cuda())
+        o.tell(loss)
+        st = g.state()
+        assert st["gen"] == o.gen and st["gen_total"] == o.gen_total
+        assert _rel(st["m"], o.m) < 1e-11
+        assert abs(st["sigma"] - o.sigma) / o.sigma < 1e-11
+        assert _rel(st["C"], o.C) < 1e-10
+        assert _rel(st["p_sigma"], o.p_sigma) < 1e-10
+        assert _rel(st["p_c"], o.p_c) < 1e-10 or np.abs(o.p_c).max() == 0
+        if block:
+            assert np.all(st["C"][:9, 9:] == 0) and np.all(st["C"][9:, :9] == 0)
+        assert np.array_equal(st["C"], st["C"].T)
+    assert n_ulp_diff <= 3
+
+
+@pytest.mark.parametrize("d,lam", [(9, 64), (18, 32)])
+def test_device_normals_match_generator_definition(api, d, lam):
+    """The kernel's Philox + FP32 Box-Muller draws equal the FP64 evaluation of
+    the same definition to FP32 rounding."""
+    sc = wl.make_scene("c1", "c1", n_instruments=d // 9)
+    tr = api.Tracker(sc, lambda_max=lam)
+    g = api.CMAES(tr, lam, np.zeros(d) + 1.0, np.ones(d), seed=(1 << 40) + 77, stream_id=5)
+    o = OCMAES(d, lam, np.zeros(d) + 1.0, np.ones(d), seed=(1 << 40) + 77, stream=5)
+    for gen in range(3):
+        g.ask()
+        zg = g.last_normals().cpu().numpy()
+        zo = o.normals()
+        assert np.all(np.abs(zg - zo) <= 2e-6 * np.maximum(1.0, np.abs(zo)))
+        loss = torch.arange(lam, dtype=torch.float32, device="cuda")
+        g.tell(loss)
+        o.ask(zo)
+        o.tell(loss.cpu().numpy())
+
+
+def test_rank_only_invariance_on_device(api):
+    sc = wl.make_scene("c1", "c1")
+    tr = api.Tracker(sc, lambda_max=16)
+    mean = np.array([0.1, 0.2, 0.3, 1, 2, 100, 0, 0, 0.4])
+    runs = []
+    # scaling by a power of two is exact in FP32, so it is strictly monotone with no ties created
+    for transform in (lambda x: x, lambda x: (x * np.float32(4.0)).astype(np.float32)):
+        g = api.CMAES(tr, 16, mean, wl.default_scales(9), sigma0=1.0, seed=77)
+        hist = []
+        for _ in range(12):
+            P = g.ask().cpu().numpy()
+            loss = transform(np.sum((P.astype(np.float64) - 0.5) ** 2, axis=1).astype(np.float32))
+            g.tell(torch.from_numpy(np.ascontiguousarray(loss, np.float32)).cuda())
+            st = g.state()
+            hist.append((st["m"].copy(), st["sigma"], st["C"].copy()))
+        runs.append(hist)
+    for a, b in zip(*runs):
+        assert np.array_equal(a[0], b[0]) and a[1] == b[1] and np.array_equal(a[2], b[2])
+
+
+def test_save_load_continues_bit_identically(api):
+    sc = wl.make_scene("c1", "c1")
+    tr = api.Tracker(sc, lambda_max=16)
+    g = api.CMAES(tr, 16, np.array([0, 0, 0, 0, 0, 100, 0, 0, 0.4]), wl.default_scales(9), seed=5)
+    f = lambda P: np.sum(P.astype(np.float64) ** 2, axis=1).astype(np.float32)
+    for _ in range(3):
+        g.tell(torch.from_numpy(f(g.ask().cpu().numpy())).cuda())
+    blob = g.save()
+    for _ in range(4):
+        g.tell(torch.from_numpy(f(g.ask().cpu().numpy())).cuda())
+    a = g.state()
+    g.load(blob)
+    for _ in range(4):
+        g.tell(torch.from_numpy(f(g.ask().cpu().numpy())).cuda())
+    b = g.state()
+    for k in ("m", "C", "p_sigma", "p_c", "best_x"):
+        assert np.array_equal(a[k], b[k])
+    assert a["sigma"] == b["sigma"] and a["gen_total"] == b["gen_total"]
+
+
+def test_track_frame_matches_oracle_tracker(api):
+    """160x128 fit, 20 generations: the device tracker's final loss and pose
+    error are statistically those of the oracle tracker (the two draw the same
+    Philox normals but round them differently, so single runs may part ways)."""
+    sc = wl.make_scene("c1", "c1")
+    tr = api.Tracker(sc, loss_kind=wl.LOSS_XOR, lambda_max=16)
+    rg, ro = [], []
+    for k in range(8):
+        rng = np.random.default_rng(1000 + k)
+        gt = wl.sample_state(rng, sc.K)
+        M = oracle.render(sc, gt)
+        init = wl.population_around(rng, gt, 1)[0].astype(np.float64)
+        x0 = oracle.eval_population(sc, init[None], M)["xor"][0]
+        o = OCMAES(9, 16, init, wl.default_scales(9), sigma0=1.0, seed=k)
+        best_o, loss_o = oracle_track_frame(o, sc, M, 20, wl.LOSS_XOR, init)
+        g = api.CMAES(tr, 16, init, wl.default_scales(9), sigma0=1.0, seed=k)
+        pose, loss_g = g.track_frame_host(M, 20)
+        # the reported estimate is what it claims to be, by the oracle's renderer
+        assert oracle.eval_population(sc, pose[None].astype(np.float64), M)["xor"][0] == loss_g
+        rg.append(loss_g / max(x0, 1))
+        ro.append(loss_o / max(x0, 1))
+    rg, ro = np.array(rg), np.array(ro)
+    assert rg.mean() <= ro.mean() + 2 * ro.std(ddof=1) / np.sqrt(len(ro)) + 0.05
+    assert np.median(rg) < 0.3
+
+
+def test_track_frame_device_equals_host_and_joint_reading(api):
+    sc = wl.make_scene("c1", "c1")
+    tr = api.Tracker(sc, loss_kind=wl.LOSS_XOR, lambda_max=16)
+    rng = np.random.default_rng(3)
+    gt = wl.sample_state(rng, sc.K)
+    M = oracle.render(sc, gt)
+    init = wl.population_around(rng, gt, 1)[0].astype(np.float64)
+    g1 = api.CMAES(tr, 16, init, wl.default_scales(9), seed=9)
+    g2 = api.CMAES(tr, 16, init, wl.default_scales(9), seed=9)
+    p1, l1 = g1.track_frame_host(M, 6)
+    Mp = tr.pack_mask(torch.from_numpy(M).cuda())
+    p2 = g2.track_frame(Mp, 6).cpu().numpy()
+    assert np.array_equal(p1, p2)
+    # joint readings replace the joints of the starting mean (forward cosine map)
+    q = np.array([0.2, -0.3, 0.5], np.float32)
+    g3 = api.CMAES(tr, 16, init, wl.default_scales(9), seed=9, sigma0=1e-9)
+    g3.track_frame_host(M, 1, joint_reading=q)
+    st = g3.state()
+    qh = [oracle.qhat_from_q(float(q[i]), sc.q_lb[i], sc.q_ub[i]) for i in range(3)]
+    assert np.allclose(st["best_x"][6:], qh, atol=1e-5)
+
+
+def test_multi_frame_warm_start(api):
+    """Each frame starts from the previous frame's estimate."""
+    sc = wl.make_scene("c1", "c1")
+    tr = api.Tracker(sc, loss_kind=wl.LOSS_XOR, lambda_max=16)
+    rng = np.random.default_rng(21)
+    gt0 = wl.sample_state(rng, sc.K)
+    traj = wl.sinusoidal_trajectory(rng, gt0, 6, amp_mm=3.0, amp_rad=0.05)
+    init = gt0 + 0.01
+    g = api.CMAES(tr, 16, init, wl.default_scales(9), seed=2)
+    o = OCMAES(9, 16, init, wl.default_scales(9), seed=2)
+    est_o = init
+    lg_all, lo_all, eg, eo = [], [], [], []
+    scales = wl.default_scales(9)
+    for f in range(6):
+        M = oracle.render(sc, traj[f])
+        pose, lg = g.track_frame_host(M, 5)
+        est_o, lo = oracle_track_frame(o, sc, M, 5, wl.LOSS_XOR, est_o)
+        lg_all.append(lg)
+        lo_all.append(lo)
+        eg.append(np.abs((pose - traj[f]) / scales).max())
+        eo.append(np.abs((est_o - traj[f]) / scales).max())
+    # follows the trajectory as well as the oracle tracker does (normalised units)
+    assert np.mean(eg) <= 2.0 * np.mean(eo) + 1.0
+    assert np.mean(lg_all) <= 1.5 * np.mean(lo_all) + 20
+
+
+@pytest.mark.parametrize("scene_kw,lam", [({"mesh": "c1", "cam": "c1"}, 16),
+                                          ({"mesh": "c1", "cam": "c1", "n_instruments": 2}, 32)])
+def test_fused_generation_equals_separate_calls(api, scene_kw, lam):
+    """cmaes_step (sample + fitness + update in one launch) is bit-identical to
+    cmaes_ask, eval_population and cmaes_tell issued separately."""
+    sc = wl.make_scene(**scene_kw)
+    d = sc.d
+    tr = api.Tracker(sc, loss_kind=wl.LOSS_ONE_MINUS_IOU, lambda_max=lam)
+    rng = np.random.default_rng(31)
+    gt = np.concatenate([wl.sample_state(rng, sc.K) for _ in range(sc.n_instruments)])
+    M = wl.corrupt_mask(oracle.render(sc, gt), rng)
+    Mp = tr.pack_mask(torch.from_numpy(M).cuda())
+    init = gt + 0.02
+    a = api.CMAES(tr, lam, init, wl.default_scales(d), seed=4, block_diag=(d == 18))
+    b = api.CMAES(tr, lam, init, wl.default_scales(d), seed=4, block_diag=(d == 18))
+    for _ in range(6):
+        a.step(Mp)
+        P = b.ask()
+        loss = tr.eval_population(P, Mp)
+        b.tell(loss)
+    sa, sb = a.state(), b.state()
+    for key in ("m", "C", "p_sigma", "p_c", "best_x"):
+        assert np.array_equal(sa[key], sb[key]), key
+    assert sa["sigma"] == sb["sigma"] and sa["best_loss"] == sb["best_loss"] and sa["gen"] == sb["gen"] == 6

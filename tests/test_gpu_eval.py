@@ -1,0 +1,235 @@
+"""Parity of the CUDA fitness path (eval_population) with the CPU oracle.
+
+Coverage counts must be bit-exact given the kernel's snapped vertices; the
+kernel's projection must agree with the FP64 oracle to 1e-4 px; its snapped
+coordinates must equal the oracle's except where 256 (u - cx) lies within
+1e-3 of a rounding boundary; losses must equal the FP32 formula applied to the
+counts.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_11404_gb300 import workload as wl
+
+from _helpers import INT32_MIN, oracle_counts_from_snapped, random_mask, tiny_scene
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_11404_gb300 import build
+    build.build()
+    from paper_2603_11404_gb300 import api as a
+    return a
+
+
+def _check_population(api, scene, P, M, loss_kind=wl.LOSS_XOR, cull=False, lambda_max=None, lambda_app=0.0,
+                      cluster=0, threads=0, fk_tol=1e-4):
+    lam = P.shape[0]
+    tr = api.Tracker(scene, loss_kind=loss_kind, lambda_max=lambda_max or max(lam, 1), cull_backfaces=cull,
+                     lambda_app=lambda_app, cluster=cluster, block_threads=threads)
+    Md = torch.from_numpy(M).cuda()
+    Mp = tr.pack_mask(Md)
+    Pd = torch.from_numpy(np.ascontiguousarray(P, np.float32)).cuda()
+    loss, counts, snap, uv = tr.eval_population_debug(Pd, Mp)
+    loss2, counts2 = tr.eval_population(Pd, Mp, counts=True)
+    torch.cuda.synchronize()
+    loss, counts, snap, uv = loss.cpu().numpy(), counts.cpu().numpy(), snap.cpu().numpy(), uv.cpu().numpy()
+    assert np.array_equal(counts, counts2.cpu().numpy())
+    assert np.array_equal(loss.view(np.int32), loss2.cpu().numpy().view(np.int32))
+    V = scene.n_verts
+    n_snap_diff = 0
+    for k in range(lam):
+        # 1) raster + reduction: bit-exact given the kernel's snapped vertices
+        s, I, m, culled, _ = oracle_counts_from_snapped(scene, snap[k], M, cull)
+        assert (counts[k] == [s, I, m, culled]).all(), (k, counts[k], (s, I, m, culled))
+        # 2) loss formula on those counts
+        want = oracle.loss_from_counts(loss_kind, s, m, I, lambda_app)
+        assert loss[k].view(np.int32) == np.float32(want).view(np.int32), (k, loss[k], want)
+        # 3) kinematics + projection against the FP64 oracle
+        for b in range(scene.n_instruments):
+            pr = oracle.project(scene, P[k, 9 * b:9 * b + 9].astype(np.float64))
+            ok = pr["flag"] == 0
+            g_flag = snap[k, b * V:(b + 1) * V, 0] == INT32_MIN
+            assert np.array_equal(g_flag, ~ok)
+            err = np.abs(uv[k, b * V:(b + 1) * V][ok] - pr["uv"][ok]).max() if ok.any() else 0.0
+            assert err <= fk_tol, (k, b, err)
+            diff = (snap[k, b * V:(b + 1) * V][ok] != pr["snap"][ok]).any(axis=1)
+            if diff.any():
+                frac = np.abs(256 * pr["uv"][ok][diff] - np.round(256 * pr["uv"][ok][diff]))
+                assert (np.abs(frac - 0.5) < 1e-3).all()
+                n_snap_diff += int(diff.sum())
+    return counts, loss, n_snap_diff
+
+
+def test_pack_mask_roundtrip(api):
+    sc = wl.make_scene("c1", "c1", K=wl.Intrinsics(200, 200, 50, 38.5, 100, 77))
+    tr = api.Tracker(sc)
+    rng = np.random.default_rng(0)
+    M = random_mask(rng, 77, 100)
+    Mp = tr.pack_mask(torch.from_numpy(M).cuda())
+    assert Mp.shape == (77, 4)
+    back = api.unpack_mask(Mp, 100).cpu().numpy()
+    assert np.array_equal(back, M)
+    pad = (Mp[:, 3].cpu().numpy().view(np.uint32) >> (100 - 96))
+    assert (pad == 0).all()  # bits past W are zero
+
+
+@pytest.mark.parametrize("rot", [wl.ROT_AXIS_ANGLE, wl.ROT_LOOKAT])
+def test_c1_population_parity(api, rot):
+    sc = wl.make_scene("c1", "c1", rot_param=rot)
+    rng = np.random.default_rng(1000)
+    gt = wl.sample_state(rng, sc.K, rot_param=rot)
+    M = oracle.render(sc, gt)
+    P = wl.population_around(rng, gt, 16)
+    counts, loss, _ = _check_population(api, sc, P, M, wl.LOSS_XOR)
+    assert counts[:, 0].min() > 100  # the tool is in view
+
+
+@pytest.mark.parametrize("loss_kind", [wl.LOSS_XOR, wl.LOSS_ONE_MINUS_IOU, wl.LOSS_MSE_APP])
+def test_loss_kinds_with_corrupted_mask(api, loss_kind):
+    sc = wl.make_scene("c1", "c1")
+    rng = np.random.default_rng(11)
+    gt = wl.sample_state(rng, sc.K)
+    M = wl.corrupt_mask(oracle.render(sc, gt), rng)
+    P = wl.population_around(rng, gt, 24)
+    _check_population(api, sc, P, M, loss_kind, lambda_app=0.37)
+
+
+def test_c2_population_parity(api):
+    """640x512, ~20k triangles, lam = 64, 1 - IoU: the metric's configuration."""
+    sc = wl.make_scene("c2", "c2")
+    rng = np.random.default_rng(2000)
+    gt = wl.sample_state(rng, sc.K)
+    M = wl.corrupt_mask(oracle.render(sc, gt), rng)
+    P = wl.population_around(rng, gt, 64)
+    counts, loss, nd = _check_population(api, sc, P, M, wl.LOSS_ONE_MINUS_IOU)
+    assert nd <= 2
+
+
+def test_bimanual_and_ragged_image(api):
+    K = wl.Intrinsics(150.0, 150.0, 50.0, 38.5, 101, 77)
+    sc = wl.make_scene("c1", "c1", n_instruments=2, K=K)
+    rng = np.random.default_rng(5)
+    gt = np.concatenate([wl.sample_state(rng, K), wl.sample_state(rng, K)])
+    M = wl.corrupt_mask(oracle.render(sc, gt), rng)
+    P = wl.population_around(rng, gt, 7)
+    _check_population(api, sc, P, M, wl.LOSS_ONE_MINUS_IOU, lambda_max=9)
+
+
+def test_single_candidate_and_cull_mode(api):
+    sc = wl.make_scene("c1", "c1")
+    rng = np.random.default_rng(6)
+    gt = wl.sample_state(rng, sc.K)
+    M = oracle.render(sc, gt)
+    P = wl.population_around(rng, gt, 1)
+    _check_population(api, sc, P, M, cull=True)
+
+
+@pytest.mark.parametrize("cluster,threads", [(1, 64), (2, 128), (8, 256), (3, 96)])
+def test_launch_shapes_agree(api, cluster, threads):
+    sc = wl.make_scene("c1", "c1")
+    rng = np.random.default_rng(7)
+    gt = wl.sample_state(rng, sc.K)
+    M = oracle.render(sc, gt)
+    P = wl.population_around(rng, gt, 5)
+    _check_population(api, sc, P, M, cluster=cluster, threads=threads)
+
+
+def test_large_triangles_warp_path(api):
+    """Near-camera close-up: triangles wider than 32 px go to the warp path."""
+    sc = wl.make_scene("c1", "c1")
+    rng = np.random.default_rng(8)
+    gt = wl.sample_state(rng, sc.K)
+    gt[3:6] = [0.0, 0.0, 25.0]
+    M = random_mask(rng, sc.K.height, sc.K.width)
+    P = wl.population_around(rng, gt, 6, sigma_mm=0.5)
+    counts, _, _ = _check_population(api, sc, P, M)
+    assert counts[:, 0].max() > 2000
+
+
+def test_full_screen_quad_and_overflow(api):
+    """Two triangles covering all W*H pixel centres, plus many large triangles
+    (more than the deferred-list capacity) to exercise the serial path."""
+    W, H, fx, z = 64, 48, 100.0, 100.0
+    # corners at pixel (-0.5, -0.5) .. (W-0.5, H-0.5) on the plane z (vertex frame = E, pose t = (0,0,z))
+    x0, x1 = (-0.5 - W / 2) * z / fx, (W - 0.5 - W / 2) * z / fx
+    y0, y1 = (-0.5 - H / 2) * z / fx, (H - 0.5 - H / 2) * z / fx
+    quad = [[x0, y0, 0], [x1, y0, 0], [x1, y1, 0], [x0, y1, 0]]
+    verts = list(quad)
+    tris = [[0, 1, 2], [0, 2, 3]]
+    rng = np.random.default_rng(9)
+    for _ in range(3000):  # ~65 % wider than 32 px: more than one CTA's 1024-entry deferred list
+        c = rng.uniform([x0, y0], [x1, y1])
+        base = len(verts)
+        for _k in range(3):
+            verts.append([c[0] + rng.uniform(-40, 40), c[1] + rng.uniform(-15, 15), 0.0])
+        tris.append([base, base + 1, base + 2])
+    sc = tiny_scene(W, H, fx, verts, tris)
+    st = np.array([[0, 0, 0, 0, 0, z, 0, 0, 0]], np.float32)
+    M = random_mask(rng, H, W)
+    counts, _, _ = _check_population(api, sc, st, M, cluster=1, threads=256)
+    assert counts[0, 0] == W * H
+
+
+def test_all_vertices_flagged_and_nan(api):
+    sc = wl.make_scene("c1", "c1")
+    rng = np.random.default_rng(10)
+    M = random_mask(rng, sc.K.height, sc.K.width)
+    P = np.zeros((3, 9), np.float32)
+    P[0, 5] = -50.0          # behind the camera
+    P[1, :] = np.nan         # non-finite state
+    P[2, 3] = 1e6; P[2, 5] = 100.0  # far outside the guard band
+    tr = api.Tracker(sc, lambda_max=3)
+    Mp = tr.pack_mask(torch.from_numpy(M).cuda())
+    loss, counts = tr.eval_population(torch.from_numpy(P).cuda(), Mp, counts=True)
+    counts = counts.cpu().numpy()
+    assert (counts[:, 0] == 0).all() and (counts[:, 1] == 0).all()
+    assert (counts[:, 3] == sc.n_tris).all()
+    assert (loss.cpu().numpy() == M.sum()).all()
+
+
+def test_empty_population_and_limits(api):
+    sc = wl.make_scene("c1", "c1")
+    tr = api.Tracker(sc, lambda_max=4)
+    Mp = torch.zeros((sc.K.height, tr.words_per_row), dtype=torch.int32, device="cuda")
+    out = tr.eval_population(torch.zeros((0, 9), dtype=torch.float32, device="cuda"), Mp)
+    assert out.numel() == 0
+    from paper_2603_11404_gb300._abi import TrkError
+    with pytest.raises(TrkError):
+        tr.eval_population(torch.zeros((5, 9), dtype=torch.float32, device="cuda"), Mp)
+
+
+def test_render_matches_oracle(api):
+    sc = wl.make_scene("c2", "c2")
+    rng = np.random.default_rng(12)
+    gt = wl.sample_state(rng, sc.K).astype(np.float32)
+    tr = api.Tracker(sc, lambda_max=1)
+    S = api.unpack_mask(tr.render(torch.from_numpy(gt).cuda()), sc.K.width).cpu().numpy()
+    Mz = np.zeros_like(S)
+    _, _, snap, _ = tr.eval_population_debug(torch.from_numpy(gt[None]).cuda(),
+                                             torch.zeros((sc.K.height, tr.words_per_row), dtype=torch.int32,
+                                                         device="cuda"))
+    _, _, _, _, S_or = oracle_counts_from_snapped(sc, snap[0].cpu().numpy(), Mz)
+    assert np.array_equal(S, S_or)
+    assert S.sum() > 1000
+
+
+def test_repeat_launches_deterministic(api):
+    sc = wl.make_scene("c2", "c2")
+    rng = np.random.default_rng(13)
+    gt = wl.sample_state(rng, sc.K)
+    M = torch.from_numpy(wl.corrupt_mask(oracle.render(sc, gt), rng)).cuda()
+    tr = api.Tracker(sc, loss_kind=wl.LOSS_ONE_MINUS_IOU, lambda_max=64)
+    Mp = tr.pack_mask(M)
+    P = torch.from_numpy(wl.population_around(rng, gt, 64)).cuda()
+    ref = tr.eval_population(P, Mp, counts=True)[1].clone()
+    for _ in range(5):
+        assert torch.equal(tr.eval_population(P, Mp, counts=True)[1], ref)
