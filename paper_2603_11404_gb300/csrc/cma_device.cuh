@@ -232,7 +232,7 @@ __device__ __forceinline__ void sandwich64(int d, const double *X, const double 
 
 // The whole update from the fitness of the last population (called by every
 // thread of one block).  y [lam*d] are the FP64 steps of that population.
-static __device__ void cma_tell_block(const CmaConst &k, CmaState *st, const double *y, const float *params,
+static __device__ __noinline__ void cma_tell_block(const CmaConst &k, CmaState *st, const double *y, const float *params,
                                const float *loss, TellSmem &S, int tid, int nt)
 {
     const int d = k.d, lam = k.lam, dd = d * d, mu = k.mu;

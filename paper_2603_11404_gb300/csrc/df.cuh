@@ -9,9 +9,9 @@
 // lanes/clk/SM against ~1.6 FP64 FMA/clk/SM, so this is how the library gets
 // near-FP64 accuracy for the per-candidate kinematics.
 //
-// sin/cos: Cody-Waite reduction by pi/2 split into three floats (the first
-// with few bits, so n * P1 is exact), then the Taylor series of sin and cos on
-// [-pi/4, pi/4] to the 17th / 18th power, evaluated by Horner's rule.
+// sin/cos: Cody-Waite reduction by pi/2 split into a float with few bits (so
+// n * P1 is exact) and a double-float remainder, then the Taylor series of sin
+// and cos on [-pi/4, pi/4] to the 17th / 18th power by Horner's rule.
 #pragma once
 
 #include <math.h>
@@ -93,62 +93,57 @@ __device__ __forceinline__ dfl df_sqrt(dfl a)
 // hi/lo split of a double done by the compiler (constant expressions only).
 #define DFL_CONST(x) dfl{(float)(x), (float)((x) - (double)(float)(x))}
 
-// 1/k! for k = 0..18 as double-float constants.
-__device__ __forceinline__ dfl inv_fact(int k)
-{
-    switch (k) {
-    case 2: return DFL_CONST(1.0 / 2.0);
-    case 3: return DFL_CONST(1.0 / 6.0);
-    case 4: return DFL_CONST(1.0 / 24.0);
-    case 5: return DFL_CONST(1.0 / 120.0);
-    case 6: return DFL_CONST(1.0 / 720.0);
-    case 7: return DFL_CONST(1.0 / 5040.0);
-    case 8: return DFL_CONST(1.0 / 40320.0);
-    case 9: return DFL_CONST(1.0 / 362880.0);
-    case 10: return DFL_CONST(1.0 / 3628800.0);
-    case 11: return DFL_CONST(1.0 / 39916800.0);
-    case 12: return DFL_CONST(1.0 / 479001600.0);
-    case 13: return DFL_CONST(1.0 / 6227020800.0);
-    case 14: return DFL_CONST(1.0 / 87178291200.0);
-    case 15: return DFL_CONST(1.0 / 1307674368000.0);
-    case 16: return DFL_CONST(1.0 / 20922789888000.0);
-    case 17: return DFL_CONST(1.0 / 355687428096000.0);
-    case 18: return DFL_CONST(1.0 / 6402373705728000.0);
-    default: return DFL_CONST(1.0);  // 0! and 1!
-    }
-}
+// Taylor coefficients as double-float constants: (-1)^j/(2j+1)! and (-1)^j/(2j)!.
+#define DFL_C2(x) {(float)(x), (float)((x) - (double)(float)(x))}
+static __constant__ float2 kSinTaylor[9] = {
+    DFL_C2(1.0), DFL_C2(-1.0 / 6.0), DFL_C2(1.0 / 120.0), DFL_C2(-1.0 / 5040.0), DFL_C2(1.0 / 362880.0),
+    DFL_C2(-1.0 / 39916800.0), DFL_C2(1.0 / 6227020800.0), DFL_C2(-1.0 / 1307674368000.0),
+    DFL_C2(1.0 / 355687428096000.0)};
+static __constant__ float2 kCosTaylor[10] = {
+    DFL_C2(1.0), DFL_C2(-1.0 / 2.0), DFL_C2(1.0 / 24.0), DFL_C2(-1.0 / 720.0), DFL_C2(1.0 / 40320.0),
+    DFL_C2(-1.0 / 3628800.0), DFL_C2(1.0 / 479001600.0), DFL_C2(-1.0 / 87178291200.0),
+    DFL_C2(1.0 / 20922789888000.0), DFL_C2(-1.0 / 6402373705728000.0)};
+#undef DFL_C2
 
-// sin and cos of a double-float angle (|x| up to ~1e4 keeps the reduction exact).
-__device__ __forceinline__ void df_sincos(dfl x, dfl &s, dfl &c)
+struct dfl2 {
+    dfl s, c;
+};
+
+// sin and cos of a double-float angle (|x| up to ~1e4 keeps the reduction
+// exact).  Kept out of line and with rolled loops: it is called from several
+// places once per candidate, so compact code matters more than a few cycles.
+static __device__ __noinline__ dfl2 df_sincos(dfl x)
 {
-    // pi/2 = P1 + P2 + P3; P1 = 201/128 has 8 significant bits
+    // pi/2 = P1 + P2 with P1 = 201/128 (8 significant bits) and P2 a double-float
     const float P1 = 1.5703125f;
     const dfl P2 = DFL_CONST(1.5707963267948966 - 1.5703125);
     const float n = rintf(__fmul_rn(x.hi, 0.636619772f));
     dfl r = df_sub(x, df_from(__fmul_rn(n, P1)));  // n * P1 exact for |n| < 2^15
     r = df_sub(r, df_mul_f(P2, n));
     const dfl u = df_mul(r, r);
-    // sin r = r * sum_{j=0..8} (-1)^j u^j / (2j+1)!,  cos r = sum_{j=0..9} (-1)^j u^j / (2j)!
-    dfl ps = inv_fact(17);
-#pragma unroll
-    for (int j = 7; j >= 0; --j) {
-        dfl cj = inv_fact(2 * j + 1);
-        ps = df_fma(ps, u, (j & 1) ? df_neg(cj) : cj);
-    }
-    dfl pc = df_neg(inv_fact(18));
-#pragma unroll
-    for (int j = 8; j >= 0; --j) {
-        dfl cj = inv_fact(2 * j);
-        pc = df_fma(pc, u, (j & 1) ? df_neg(cj) : cj);
-    }
+    // sin r = r * S(u), S(u) = sum_{j=0..8} s_j u^j;  cos r = C(u) = sum_{j=0..9} c_j u^j,
+    // u = r^2, evaluated by Estrin's scheme (independent pairs, then powers
+    // u^2, u^4, u^8) to keep the dependent chain short
+    const dfl u2 = df_mul(u, u), u4 = df_mul(u2, u2), u8 = df_mul(u4, u4);
+#define TS(j) dfl{kSinTaylor[j].x, kSinTaylor[j].y}
+#define TC(j) dfl{kCosTaylor[j].x, kCosTaylor[j].y}
+    dfl s01 = df_fma(TS(1), u, TS(0)), s23 = df_fma(TS(3), u, TS(2));
+    dfl s45 = df_fma(TS(5), u, TS(4)), s67 = df_fma(TS(7), u, TS(6));
+    dfl c01 = df_fma(TC(1), u, TC(0)), c23 = df_fma(TC(3), u, TC(2));
+    dfl c45 = df_fma(TC(5), u, TC(4)), c67 = df_fma(TC(7), u, TC(6)), c89 = df_fma(TC(9), u, TC(8));
+    dfl s03 = df_fma(s23, u2, s01), s47 = df_fma(s67, u2, s45);
+    dfl c03 = df_fma(c23, u2, c01), c47 = df_fma(c67, u2, c45);
+    dfl ps = df_fma(TS(8), u8, df_fma(s47, u4, s03));
+    dfl pc = df_fma(c89, u8, df_fma(c47, u4, c03));
+#undef TS
+#undef TC
     dfl sr = df_mul(ps, r);
     dfl cr = pc;
     int q = ((int)n) & 3;
     dfl ss = (q & 1) ? cr : sr, cc = (q & 1) ? sr : cr;
     if (q == 1 || q == 2) cc = df_neg(cc);  // cos: +c, -s, -c, +s
     if (q >= 2) ss = df_neg(ss);            // sin: +s, +c, -s, -c
-    s = ss;
-    c = cc;
+    return {ss, cc};
 }
 
 __device__ __forceinline__ double df_to_double(dfl a) { return (double)a.hi + (double)a.lo; }

@@ -42,14 +42,14 @@ __device__ __forceinline__ dfl dot3(dfl a0, dfl b0, dfl a1, dfl b1, dfl a2, dfl 
 }
 
 // Elementary rotation about x, y or z (identity for TRK_AXIS_NONE).
-__device__ __forceinline__ void rot_elem_df(int axis, dfl a, dfl R[9])
+static __device__ __noinline__ void rot_elem_df(int axis, dfl a, dfl R[9])
 {
     const dfl one = df_from(1.0f), zero = df_from(0.0f);
 #pragma unroll
     for (int i = 0; i < 9; ++i) R[i] = (i % 4 == 0) ? one : zero;
     if (axis == TRK_AXIS_NONE) return;
-    dfl s, c;
-    df_sincos(a, s, c);
+    dfl2 sc = df_sincos(a);
+    dfl s = sc.s, c = sc.c;
     if (axis == TRK_AXIS_X) { R[4] = c; R[5] = df_neg(s); R[7] = s; R[8] = c; }
     if (axis == TRK_AXIS_Y) { R[0] = c; R[2] = s; R[6] = df_neg(s); R[8] = c; }
     if (axis == TRK_AXIS_Z) { R[0] = c; R[1] = df_neg(s); R[3] = s; R[4] = c; }
@@ -68,7 +68,7 @@ __device__ __forceinline__ void mul3_df(const dfl A[9], const dfl B[9], dfl C[9]
 
 // Pose rotation of T_r^c: axis-angle, R = cos(t) I + sin(t) [k]x + (1 - cos(t)) k k^T
 // with t = |r|, k = r / t (I + [r]x when t < 1e-8); or look-at Ry(gamma) Rx(alpha) Rz(beta).
-__device__ void pose_rotation_df(int rot_param, const float *r, dfl R[9])
+static __device__ __noinline__ void pose_rotation_df(int rot_param, const float *r, dfl R[9])
 {
     if (rot_param == TRK_ROT_LOOKAT) {
         dfl Ry[9], Rx[9], Rz[9], T[9];
@@ -88,9 +88,10 @@ __device__ void pose_rotation_df(int rot_param, const float *r, dfl R[9])
         R[6] = df_neg(r1); R[7] = r0; R[8] = one;
         return;
     }
-    dfl k[3] = {df_div(r0, t), df_div(r1, t), df_div(r2, t)};
-    dfl s, c;
-    df_sincos(t, s, c);
+    dfl it = df_div(df_from(1.0f), t);
+    dfl k[3] = {df_mul(r0, it), df_mul(r1, it), df_mul(r2, it)};
+    dfl2 sc = df_sincos(t);
+    dfl s = sc.s, c = sc.c;
     dfl c1 = df_sub(one, c);
     dfl Kx[9] = {df_from(0.f), df_neg(k[2]), k[1], k[2], df_from(0.f), df_neg(k[0]), df_neg(k[1]), k[0], df_from(0.f)};
 #pragma unroll
@@ -118,8 +119,7 @@ __device__ void compose_frames_warp(const ChainDev &ch, const CamDev &cam, const
     const int nF = ch.n_frames;
     if (lane < 3) {
         dfl arg = df_mul(df_sub(df_from(st[6 + lane]), dfc(ch.lb_df[lane])), dfc(ch.pi_over_range_df[lane]));
-        dfl sn, cs;
-        df_sincos(arg, sn, cs);
+        dfl cs = df_sincos(arg).c;
         dfl q = df_fma(dfc(ch.half_range_df[lane]), df_sub(df_from(1.0f), cs), dfc(ch.lb_df[lane]));
         qs[lane] = make_float2(q.hi, q.lo);
     }
@@ -457,8 +457,7 @@ __global__ void __launch_bounds__(256, 4) k_eval(EvalArgs a)
             if (a.uv_dbg) a.uv_dbg[(size_t)c * NV + idx1] = uv1;
         }
     }
-    __threadfence();
-    cluster.sync();
+    cluster.sync();  // arrive.release / wait.acquire: the snapped vertices are visible cluster-wide
 
     // ---- phase 2: triangles -> this CTA's bitmap, next triangle's loads in flight ----
     int culled = 0;
