@@ -164,6 +164,41 @@ trk_status eval_population_debug(trk_tracker *t, const float *params_dev, int32_
                                  const uint32_t *mask_packed_dev, float *loss_dev, int32_t *counts_dev,
                                  int32_t *snap_dev, float *uv_dev, void *stream);
 
+/* Largest lam * n_instruments * n_verts that eval_population_noalloc accepts
+ * (the size, in snapped vertices, of its fixed scratch array: 16 MiB). */
+#define TRK_NOALLOC_MAX_SNAP (1 << 21)
+
+/* Allocation-free fitness evaluation.  The paper has no counterpart: this is
+ * a service for callers that must not allocate device memory at the point
+ * where they evaluate a population -- code running inside another framework's
+ * memory pool or arena (which forbids cudaMalloc behind its back), real-time
+ * control loops that cannot take the allocator's locks or latency, and hosts
+ * that only hand out pre-registered buffers.  It computes exactly what
+ * eval_population computes, but needs no tracker: the caller passes the mesh,
+ * chain, camera and configuration together with the population, and the
+ * call allocates nothing (no cudaMalloc, cudaFree or allocating library
+ * routine).  The one scratch buffer the kernel needs (every candidate's
+ * snapped vertices) is a fixed device array inside this library, 16 MiB,
+ * held by every GPU that loads the library until the process exits.
+ *   verts_dev [n_verts*4] FP32: x, y, z (mm) and the vertex's frame index
+ *     stored as a float; tris_dev [n_tris*4] int32: three vertex indices and
+ *     one unused word.  Indices are NOT checked (they are in device memory):
+ *     they must lie in [0, n_verts) and frames in [0, n_frames).
+ *   chain, K, cfg: host structs as for tracker_create (cfg.lambda_max is
+ *     ignored); params_dev, lam, mask_packed_dev, loss_dev, counts_dev: as
+ *     for eval_population.
+ * Errors: TRK_EINVAL (reason in tracker_last_error()) for bad arguments or
+ * lam * n_instruments * n_verts > TRK_NOALLOC_MAX_SNAP; TRK_ECUDA.
+ * The first call on each device looks up the scratch array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * Every call shares the array: calls whose kernels can overlap on the GPU
+ * (other streams, other host threads) race on it and must be serialised by
+ * the caller.  Asynchronous on `stream`. */
+trk_status eval_population_noalloc(const float *verts_dev, int32_t n_verts, const int32_t *tris_dev, int32_t n_tris,
+                                   const trk_chain *chain, const trk_intrinsics *K, const trk_config *cfg,
+                                   const float *params_dev, int32_t lam, const uint32_t *mask_packed_dev,
+                                   float *loss_dev, int32_t *counts_dev, void *stream);
+
 /* Render the union silhouette of one state into a packed bitmap
  * (silhouette_dev [H*ceil(W/32)] words): used to make synthetic observations
  * and for inspection, not by the fitness path.  Asynchronous. */

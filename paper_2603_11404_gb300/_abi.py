@@ -77,6 +77,7 @@ SIGNATURES = {
     "track_frame_host": [P, P, I32, P, P, P, P],
     "cmaes_save": [P, P, P, P],
     "cmaes_load": [P, P, C.c_size_t, P],
+    "eval_population_noalloc": [P, I32, P, I32, P, P, P, P, I32, P, P, P, P],
 }
 
 _lib = None

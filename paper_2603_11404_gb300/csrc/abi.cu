@@ -41,6 +41,8 @@ inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s
 
 }  // namespace
 
+void trk::set_last_error(const char *msg) { g_last_error = msg; }
+
 struct trk_tracker {
     int device = 0;
     ChainDev ch{};

@@ -118,6 +118,7 @@ size_t tell_smem_bytes();
 cudaError_t launch_pack_mask(const uint8_t *mask, uint32_t *packed, int W, int H, int Wq, cudaStream_t s);
 size_t eval_smem_bytes(const EvalArgs &a);
 cudaError_t prepare_eval(size_t smem);
+void set_last_error(const char *msg);  // the text tracker_last_error() returns
 int eval_max_threads();
 
 cudaError_t launch_cma_reset(const CmaConst *k, CmaState *st, const double *mean_dev, bool from_est,
