@@ -176,6 +176,9 @@ template <typename T>
 __device__ __forceinline__ void jacobi_round_apply(int d, int np, const int *rp, const int *rq, const T *rc,
                                                    const T *rs, const T *A, T *A2, const T *V, T *V2, int tid, int nt)
 {
+    // consecutive items go to different warps, so a block of several warps
+    // spreads the work over all of its sub-partitions' pipes
+    if (nt > 32 && nt % 32 == 0) tid = (tid & 31) * (nt >> 5) + (tid >> 5);
     for (int e = tid; e < np * np; e += nt) {  // 2x2 block (P, Q)
         int P = e / np, Q = e - P * np;
         int ip[2] = {rp[P], rq[P]}, jq[2] = {rp[Q], rq[Q]};
@@ -232,10 +235,14 @@ __device__ __forceinline__ void sandwich64(int d, const double *X, const double 
 
 // The whole update from the fitness of the last population (called by every
 // thread of one block).  y [lam*d] are the FP64 steps of that population.
-static __device__ __noinline__ void cma_tell_block(const CmaConst &k, CmaState *st, const double *y, const float *params,
-                               const float *loss, TellSmem &S, int tid, int nt)
+// DC is the dimension as a compile-time constant (0 = read k.d at run time):
+// the index arithmetic below divides by d and by the number of Jacobi pairs,
+// which is cheap only for constant divisors.
+template <int DC>
+__device__ __forceinline__ void cma_tell_impl(const CmaConst &k, CmaState *st, const double *y, const float *params,
+                                              const float *loss, TellSmem &S, int tid, int nt)
 {
-    const int d = k.d, lam = k.lam, dd = d * d, mu = k.mu;
+    const int d = DC ? DC : k.d, lam = k.lam, dd = d * d, mu = k.mu;
     for (int i = tid; i < lam; i += nt) {
         float v = loss[i];
         S.sl[i] = isnan(v) ? INFINITY : v;
@@ -319,22 +326,40 @@ static __device__ __noinline__ void cma_tell_block(const CmaConst &k, CmaState *
         S.pc[tid] = v;
     }
     __syncthreads();
-    // C <- decay C + c1 p_c p_c^T + c_mu sum w_r y_r y_r^T (block form: zero off-diagonal blocks)
+    // C <- decay C + c1 p_c p_c^T + c_mu sum w_r y_r y_r^T (block form: zero off-diagonal
+    // blocks); the rank-mu sum runs as 4 deterministic partial chains held in
+    // the (still unused) A, A2, V, V2 buffers
     const double c1 = k.c_1, cmu = k.c_mu;
     const double decay = 1.0 + c1 * ((1.0 - hs) * cc * (2.0 - cc)) - c1 - cmu;
-    for (int e = tid; e < dd; e += nt) {
-        int i = e / d, j = e - i * d;
-        if (j < i) continue;
-        double v = 0.0;
-        if (!(k.block && (i / k.block != j / k.block))) {
+    {
+        double *part4[4] = {S.A, S.A2, S.V, S.V2};
+        const int rchunk = (mu + 3) / 4;
+        for (int e = tid; e < 4 * dd; e += nt) {
+            int pr = e / dd, ij = e - pr * dd, i = ij / d, j = ij - i * d;
+            if (j < i) continue;
             double rmu = 0.0;
-            for (int r = 0; r < mu; ++r) rmu = __fma_rn(S.w[r] * YSEL(r, i), YSEL(r, j), rmu);
-            v = __dadd_rn(__dadd_rn(__dmul_rn(decay, S.C[e]), __dmul_rn(c1, S.pc[i] * S.pc[j])), __dmul_rn(cmu, rmu));
+            int r1 = min(mu, (pr + 1) * rchunk);
+            for (int r = pr * rchunk; r < r1; ++r) rmu = __fma_rn(S.w[r] * YSEL(r, i), YSEL(r, j), rmu);
+            part4[pr][ij] = rmu;
         }
-        S.A[i * d + j] = v;
-        S.A[j * d + i] = v;
+        __syncthreads();
+        for (int e = tid; e < dd; e += nt) {
+            int i = e / d, j = e - i * d;
+            if (j < i) continue;
+            double v = 0.0;
+            if (!(k.block && (i / k.block != j / k.block))) {
+                double rmu = __dadd_rn(__dadd_rn(part4[0][e], part4[1][e]), __dadd_rn(part4[2][e], part4[3][e]));
+                v = __dadd_rn(__dadd_rn(__dmul_rn(decay, S.C[e]), __dmul_rn(c1, S.pc[i] * S.pc[j])), __dmul_rn(cmu, rmu));
+            }
+            part4[0][e] = v;  // the same thread read part4[*][e] above
+        }
+        __syncthreads();
+        for (int e = tid; e < dd; e += nt) {
+            int i = e / d, j = e - i * d;
+            if (j < i) S.A[e] = S.A[j * d + i];
+        }
+        __syncthreads();
     }
-    __syncthreads();
     for (int e = tid; e < dd; e += nt) {
         S.C[e] = S.A[e];
         st->C[e] = S.A[e];
@@ -366,37 +391,43 @@ static __device__ __noinline__ void cma_tell_block(const CmaConst &k, CmaState *
         S.Af[e] = acc;
     }
     __syncthreads();
-    float *Af = S.Af, *Af2 = S.Af2, *Vf = S.Vf, *Vf2 = S.Vf2;
-    for (int sweep = 0; sweep < 10; ++sweep) {
-        // until the off-diagonal is at FP32 rounding level (relative 1e-6, or
-        // 4e-7 of the largest diagonal entry): FP64 sweeps finish the job
-        float amax = 0.0f;
-        for (int i = 0; i < d; ++i) amax = fmaxf(amax, fabsf(Af[i * d + i]));
-        const float floor2 = (4e-7f * amax) * (4e-7f * amax);
-        int off = 0;
-        for (int e = tid; e < dd; e += nt) {
-            int i = e / d, j = e - i * d;
-            if (j > i && Af[e] * Af[e] > 1e-12f * fabsf(Af[i * d + i] * Af[j * d + j]) + floor2) off = 1;
-        }
-        if (!__syncthreads_or(off)) break;
-        for (int s = 0; s < n2r - 1; ++s) {
-            if (tid < np) {
-                int p, q;
-                rr_pair(n2r, s, tid, p, q);
-                float c = 1.0f, sn = 0.0f;
-                if (p < d && q < d) jacobi_angle_f32(Af[q * d + q] - Af[p * d + p], Af[p * d + q], c, sn);
-                S.rp[tid] = p;
-                S.rq[tid] = q;
-                S.rc[tid] = c;
-                S.rs[tid] = sn;
+    {
+        float *Af = S.Af, *Af2 = S.Af2, *Vf = S.Vf, *Vf2 = S.Vf2;
+        for (int sweep = 0; sweep < 10; ++sweep) {
+            // until the off-diagonal is at FP32 rounding level (relative 1e-6, or
+            // 4e-7 of the largest diagonal entry): the FP64 sweep finishes the job
+            float amax = 0.0f;
+            for (int i = 0; i < d; ++i) amax = fmaxf(amax, fabsf(Af[i * d + i]));
+            const float floor2 = (4e-7f * amax) * (4e-7f * amax);
+            int off = 0;
+            for (int e = tid; e < dd; e += nt) {
+                int i = e / d, j = e - i * d;
+                if (j > i && Af[e] * Af[e] > 1e-12f * fabsf(Af[i * d + i] * Af[j * d + j]) + floor2) off = 1;
             }
-            __syncthreads();
-            jacobi_round_apply<float>(d, np, S.rp, S.rq, S.rc, S.rs, Af, Af2, Vf, Vf2, tid, nt);
-            __syncthreads();
-            float *t = Af; Af = Af2; Af2 = t;
-            t = Vf; Vf = Vf2; Vf2 = t;
+            if (!__syncthreads_or(off)) break;
+            for (int s2 = 0; s2 < n2r - 1; ++s2) {
+                if (tid < np) {
+                    int p, q;
+                    rr_pair(n2r, s2, tid, p, q);
+                    float c = 1.0f, sn = 0.0f;
+                    if (p < d && q < d) jacobi_angle_f32(Af[q * d + q] - Af[p * d + p], Af[p * d + q], c, sn);
+                    S.rp[tid] = p;
+                    S.rq[tid] = q;
+                    S.rc[tid] = c;
+                    S.rs[tid] = sn;
+                }
+                __syncthreads();
+                jacobi_round_apply<float>(d, np, S.rp, S.rq, S.rc, S.rs, Af, Af2, Vf, Vf2, tid, nt);
+                __syncthreads();
+                float *t = Af; Af = Af2; Af2 = t;
+                t = Vf; Vf = Vf2; Vf2 = t;
+            }
         }
+        if (Vf != S.Vf)  // an odd number of rounds left the basis in S.Vf2
+            for (int e = tid; e < dd; e += nt) S.Vf[e] = S.Vf2[e];
     }
+    __syncthreads();
+    const float *Vf = S.Vf;
     // ---- phase 2: V = orth(B Vf) in FP64 (two Newton-Schulz polar steps,
     //      V <- V (3 I - V^T V) / 2, taking 1e-6 to FP64 rounding) ----
     double *V = S.V, *V2 = S.V2, *A = S.A, *A2 = S.A2;
@@ -425,15 +456,12 @@ static __device__ __noinline__ void cma_tell_block(const CmaConst &k, CmaState *
         double *t = V; V = V2; V2 = t;
     }
     sandwich64(d, V, S.C, A2, A, tid, nt);  // A = V^T C V
-    // ---- phase 3: FP64 Jacobi sweeps (FP32 angles, FP64-normalised rotations) ----
+    // ---- phase 3: one FP64 Jacobi sweep (FP32 angles, FP64-normalised rotations):
+    //      the FP32 pass left off-diagonals at ~1e-6 relative, each rotation
+    //      removes all but ~1e-7 of its entry and the sweep's cross terms are
+    //      second order, so one sweep reaches ~1e-12 relative ----
     int sweeps64 = 0;
-    for (; sweeps64 < 8; ++sweeps64) {
-        int off = 0;
-        for (int e = tid; e < dd; e += nt) {
-            int i = e / d, j = e - i * d;
-            if (j > i && A[e] * A[e] > 1e-24 * fabs(A[i * d + i] * A[j * d + j])) off = 1;  // 1e-12 relative
-        }
-        if (!__syncthreads_or(off)) break;
+    for (; sweeps64 < 1; ++sweeps64) {
         for (int s = 0; s < n2r - 1; ++s) {
             if (tid < np) {
                 int p, q;
@@ -488,6 +516,15 @@ static __device__ __noinline__ void cma_tell_block(const CmaConst &k, CmaState *
         st->C_inv_half[e] = ih;
         st->B[e] = V[e];
     }
+}
+
+static __device__ __noinline__ void cma_tell_block(const CmaConst &k, CmaState *st, const double *y,
+                                                   const float *params, const float *loss, TellSmem &S, int tid,
+                                                   int nt)
+{
+    if (k.d == 9) cma_tell_impl<9>(k, st, y, params, loss, S, tid, nt);
+    else if (k.d == 18) cma_tell_impl<18>(k, st, y, params, loss, S, tid, nt);
+    else cma_tell_impl<0>(k, st, y, params, loss, S, tid, nt);
 }
 
 // Frame epilogue: the frame's best candidate becomes the estimate.

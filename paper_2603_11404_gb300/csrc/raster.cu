@@ -442,7 +442,7 @@ __global__ void __launch_bounds__(256, 4) k_eval(EvalArgs a)
     for (int idx0 = gtid; idx0 < NV; idx0 += 2 * gstride) {
         const int idx1 = idx0 + gstride;
         const bool has1 = idx1 < NV;
-        int b0 = idx0 / a.V, b1 = has1 ? idx1 / a.V : b0;
+        int b0 = idx0 >= a.V, b1 = has1 ? (idx1 >= a.V) : b0;  // instrument (at most 2): no division
         float4 p0 = a.verts[idx0 - b0 * a.V];
         float4 p1 = has1 ? a.verts[idx1 - b1 * a.V] : p0;
         float2 uv0, uv1;
@@ -468,7 +468,7 @@ __global__ void __launch_bounds__(256, 4) k_eval(EvalArgs a)
         int bc = 0, bn = 0;
         int2 v0 = make_int2(0, 0), v1 = v0, v2 = v0;
         if (tt < NT) {
-            bc = tt / a.T;
+            bc = tt >= a.T;  // instrument (at most 2): no division
             tri_c = a.tris[tt - bc * a.T];
             const int2 *sv = snapc + bc * a.V;
             // written by other CTAs of the cluster in phase 1: read through L2
@@ -478,7 +478,7 @@ __global__ void __launch_bounds__(256, 4) k_eval(EvalArgs a)
         }
         int tn = tt + gstride;
         if (tn < NT) {
-            bn = tn / a.T;
+            bn = tn >= a.T;
             tri_n = a.tris[tn - bn * a.T];
         }
         while (tt < NT) {
@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(256, 4) k_eval(EvalArgs a)
                 w2 = __ldcg(svn + tri_n.z);
             }
             if (tnn < NT) {
-                bnn = tnn / a.T;
+                bnn = tnn >= a.T;
                 tri_nn = a.tris[tnn - bnn * a.T];
             }
             TriSetup t;
@@ -521,7 +521,7 @@ __global__ void __launch_bounds__(256, 4) k_eval(EvalArgs a)
     const int nbig = min(sacc[4], kBigListCap);
     for (int e = warp; e < nbig; e += nwarp) {
         int tt = big[e];
-        int b = tt / a.T;
+        int b = tt >= a.T;
         int4 tri = a.tris[tt - b * a.T];
         const int2 *sv = snapc + b * a.V;
         TriSetup t;
