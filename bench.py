@@ -39,6 +39,21 @@ LAM, GENS = 64, 5
 SEED = 2000
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 ALGO_OPS_PER_VERT, ALGO_OPS_PER_TRI, ALGO_OPS_PER_BBOX_PX = 16, 40, 4
+# DRAM bytes (read + write) of one plain k_eval launch at 640x512, lambda = 64, from
+# ncu (profiles/k_eval_640x512.md), valid for the kernel sources with this digest;
+# reported as null once those sources change.
+KEVAL_TRAFFIC_BYTES = 614656
+KEVAL_TRAFFIC_DIGEST = None  # filled in when the capture is committed
+KERNEL_SOURCES = ("raster.cu", "cma_device.cuh", "df.cuh", "internal.cuh")
+
+
+def _kernel_digest():
+    import hashlib
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2603_11404_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def _args():
@@ -49,6 +64,9 @@ def _args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--profile-target", action="store_true",
+                   help="run a short fixed launch sequence for ncu (2 warm-up + 3 plain k_eval launches at "
+                        "640x512, lambda = 64, then 3 fused generations) and exit")
     return p.parse_args()
 
 
@@ -235,8 +253,9 @@ def run_ours(a):
     ops_per_launch = ops / R
     achieved = ops_per_launch / (float(k_ms.mean()) / 1e3)
     peak = _alu_peak()
+    traffic = KEVAL_TRAFFIC_BYTES if KEVAL_TRAFFIC_DIGEST == _kernel_digest() else None
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic, "traffic_unit": "DRAM bytes per launch (ncu)",
                 "kernel": "k_eval (fused FK/projection/snap + raster + popcount)",
                 "kernel_ms": float(k_ms.mean()), "ops_per_launch": ops_per_launch,
                 "peak_source": "152 SMs x 64 INT32 ALU lanes/clk x 2070 MHz (derived; LOP3 probe 20.0 Tops/s)"}
@@ -356,8 +375,31 @@ def run_reference(a):
     print(json.dumps(out), flush=True)
 
 
+def run_profile_target():
+    """A short, fixed launch sequence for ncu captures of the fitness kernel."""
+    import torch
+
+    from paper_2603_11404_gb300 import api, build
+    build.build()
+    sc, traj, init = _workload(0, 1)
+    tr = api.Tracker(sc, loss_kind=wl.LOSS_ONE_MINUS_IOU, lambda_max=LAM)
+    S = api.unpack_mask(tr.render(torch.from_numpy(traj[0].astype(np.float32)).cuda()), sc.K.width).cpu().numpy()
+    Mp = tr.pack_mask(torch.from_numpy(_corrupt(S, 0, 0)).cuda())
+    P = torch.from_numpy(wl.population_around(np.random.default_rng(SEED), traj[0], LAM)).cuda()
+    for _ in range(5):  # launches 2..4 of k_eval (0-based, after the render) are the measured ones
+        tr.eval_population(P, Mp)
+    es = api.CMAES(tr, LAM, traj[0], wl.default_scales(9), sigma0=1.0, seed=SEED)
+    for _ in range(3):
+        es.step(Mp)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_target": "k_eval 640x512 lambda=64", "kernel_digest": _kernel_digest()}))
+
+
 if __name__ == "__main__":
     args = _args()
+    if args.profile_target:
+        run_profile_target()
+        raise SystemExit(0)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":

@@ -286,6 +286,56 @@ trk_status track_frame_host(trk_cmaes *es, const uint8_t *mask_host, int32_t gen
                             const float *joint_reading_host, float *pose_out_host, float *best_loss_out,
                             void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Heterogeneous batches: many instances (one- or two-instrument scenes with
+ * their own meshes, image sizes and population sizes) in one persistent launch
+ * per generation.  Not a paper feature: the paper tracks one scene per call;
+ * batching serves several scenes or camera streams per GPU pass.
+ * ------------------------------------------------------------------------- */
+typedef struct trk_batch trk_batch;
+
+/* n instances; instance i uses trackers[i] and, if optimisers is not NULL,
+ * optimisers[i] (created on trackers[i]) for its populations; otherwise lam[i]
+ * gives its population size.  Trackers may be shared between instances (the
+ * batch owns its scratch).  cluster (CTAs per candidate, 1..8) and threads
+ * (per CTA, multiple of 32, <= 256) may be 0 for the default (8, 256).
+ * Synchronous (allocates and uploads the batch's tables). */
+trk_status batch_create(trk_tracker *const *trackers, trk_cmaes *const *optimisers, const int32_t *lam, int32_t n,
+                        int32_t cluster, int32_t threads, trk_batch **out);
+trk_status batch_destroy(trk_batch *b);
+
+/* Launch shape of the persistent kernel: set, or read back (n_clusters = the
+ * co-resident clusters of the persistent grid). */
+trk_status batch_set_launch(trk_batch *b, int32_t cluster, int32_t threads);
+trk_status batch_get_launch(const trk_batch *b, int32_t *cluster, int32_t *threads, int32_t *n_clusters);
+
+/* Fitness of every instance in one persistent launch: host arrays of n device
+ * pointers (params [lam_i*d_i], packed masks, loss [lam_i] or a NULL array,
+ * counts [lam_i*4] or a NULL array), results identical to eval_population per
+ * instance.  Asynchronous on `stream` (the small descriptor upload is staged
+ * from host memory before the call returns). */
+trk_status batch_eval(trk_batch *b, const float *const *params_dev, const uint32_t *const *masks_dev,
+                      float *const *loss_dev, int32_t *const *counts_dev, void *stream);
+
+/* One tracked frame of every instance (the batch must have optimisers): reset
+ * around each instance's estimate, `generations` x (one persistent fitness
+ * launch that also samples + one launch running every instance's CMA-ES
+ * update), then each frame's best becomes its estimate and is written to
+ * poses_dev[i] [d_i].  With use_graph != 0 the sequence is recorded once as a
+ * CUDA graph and replayed (re-recorded when `generations` changes).  Results
+ * are identical to track_frame_device on each instance alone.  Waits for the
+ * stream's previous work, then enqueues asynchronously. */
+trk_status batch_track_frame(trk_batch *b, const uint32_t *const *masks_dev, int32_t generations,
+                             float *const *poses_dev, int32_t use_graph, void *stream);
+
+/* Autotuner: times the persistent fitness launch for every launch shape
+ * (CTAs per candidate 1, 2, 4, 8 x threads 128, 256) on this batch's own
+ * populations (params_dev per instance, or NULL to use the optimisers'
+ * buffers) and masks, keeps the fastest and reports it (any output may be
+ * NULL; us_out = microseconds per launch).  Synchronises the stream. */
+trk_status batch_autotune(trk_batch *b, const float *const *params_dev, const uint32_t *const *masks_dev,
+                          int32_t reps, int32_t *cluster_out, int32_t *threads_out, float *us_out, void *stream);
+
 /* Checkpoint: the whole optimiser state as a plain blob.  cmaes_save with
  * blob = NULL sets *n to the size needed.  A loaded optimiser continues
  * bit-identically.  Both synchronise the stream. */

@@ -78,6 +78,13 @@ SIGNATURES = {
     "cmaes_save": [P, P, P, P],
     "cmaes_load": [P, P, C.c_size_t, P],
     "eval_population_noalloc": [P, I32, P, I32, P, P, P, P, I32, P, P, P, P],
+    "batch_create": [P, P, P, I32, I32, I32, P],
+    "batch_destroy": [P],
+    "batch_set_launch": [P, I32, I32],
+    "batch_get_launch": [P, P, P, P],
+    "batch_eval": [P, P, P, P, P, P],
+    "batch_track_frame": [P, P, I32, P, I32, P],
+    "batch_autotune": [P, P, P, I32, P, P, P, P],
 }
 
 _lib = None

@@ -257,3 +257,73 @@ class CMAES:
     def load(self, blob: bytes, stream=None):
         buf = (C.c_char * len(blob)).from_buffer_copy(blob)
         call("cmaes_load", self.h, buf, len(blob), _stream(stream))
+
+
+def _ptr_array(tensors):
+    arr = (C.c_void_p * len(tensors))()
+    for i, t in enumerate(tensors):
+        arr[i] = None if t is None else t.data_ptr()
+    return arr
+
+
+class Batch:
+    """Heterogeneous batch: batch_create / batch_eval / batch_track_frame / batch_autotune."""
+
+    def __init__(self, trackers, optimisers=None, lams=None, cluster: int = 0, threads: int = 0):
+        self.trackers = list(trackers)
+        self.optimisers = list(optimisers) if optimisers is not None else None
+        n = len(self.trackers)
+        th = (C.c_void_p * n)(*[t.h for t in self.trackers])
+        oh = None
+        lam = None
+        if self.optimisers is not None:
+            oh = (C.c_void_p * n)(*[o.h for o in self.optimisers])
+            self.lams = [o.lam for o in self.optimisers]
+        else:
+            self.lams = [int(l) for l in lams]
+            lam = (C.c_int32 * n)(*self.lams)
+        h = C.c_void_p()
+        call("batch_create", th, oh, lam, n, int(cluster), int(threads), C.byref(h))
+        self.h = h
+        self.n = n
+
+    def close(self):
+        if getattr(self, "h", None):
+            call("batch_destroy", self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def launch(self):
+        c, t, nc = C.c_int32(), C.c_int32(), C.c_int32()
+        call("batch_get_launch", self.h, C.byref(c), C.byref(t), C.byref(nc))
+        return c.value, t.value, nc.value
+
+    def set_launch(self, cluster: int, threads: int):
+        call("batch_set_launch", self.h, int(cluster), int(threads))
+
+    def eval(self, params, masks, stream=None):
+        """Per-instance params [lam_i, d_i] and packed masks -> (losses, counts)."""
+        losses = [torch.empty(p.shape[0], dtype=torch.float32, device="cuda") for p in params]
+        counts = [torch.empty((p.shape[0], 4), dtype=torch.int32, device="cuda") for p in params]
+        call("batch_eval", self.h, _ptr_array(params), _ptr_array(masks), _ptr_array(losses), _ptr_array(counts),
+             _stream(stream))
+        return losses, counts
+
+    def track_frame(self, masks, generations: int, poses=None, use_graph: bool = True, stream=None):
+        if poses is None:
+            poses = [torch.empty(t.d, dtype=torch.float32, device="cuda") for t in self.trackers]
+        self._keep = (list(masks), poses)
+        call("batch_track_frame", self.h, _ptr_array(masks), int(generations), _ptr_array(poses), int(bool(use_graph)),
+             _stream(stream))
+        return poses
+
+    def autotune(self, masks, params=None, reps: int = 5, stream=None):
+        c, t, us = C.c_int32(), C.c_int32(), C.c_float()
+        call("batch_autotune", self.h, None if params is None else _ptr_array(params), _ptr_array(masks), int(reps),
+             C.byref(c), C.byref(t), C.byref(us), _stream(stream))
+        return c.value, t.value, us.value

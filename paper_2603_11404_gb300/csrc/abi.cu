@@ -43,37 +43,6 @@ inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s
 
 void trk::set_last_error(const char *msg) { g_last_error = msg; }
 
-struct trk_tracker {
-    int device = 0;
-    ChainDev ch{};
-    CamDev cam{};
-    trk_config cfg{};
-    int V = 0, T = 0, d = 0;
-    float4 *verts = nullptr;
-    int4 *tris = nullptr;
-    int2 *snap = nullptr;       // scratch [lambda_max * n_inst * V]
-    uint32_t *zero_mask = nullptr;
-    LaunchCfg lc{};
-};
-
-struct trk_cmaes {
-    trk_tracker *t = nullptr;
-    CmaConst hk{};
-    CmaConst *k = nullptr;      // device copy
-    CmaState *st = nullptr;
-    double *y = nullptr;        // [lam*d]
-    double *z = nullptr;        // [lam*d] normals of the last population
-    float *params = nullptr;    // [lam*d]
-    float *loss = nullptr;      // [lam]
-    double *mean0 = nullptr;    // [d] creation mean (physical)
-    uint8_t *mask_bytes = nullptr;
-    uint32_t *mask_packed = nullptr;
-    float *joint = nullptr;     // [3*n_inst]
-    float *pose = nullptr;      // [d]
-    unsigned *done = nullptr;   // CTA ticket counter of the fused generation kernel
-    int lam = 0, d = 0;
-};
-
 extern "C" {
 
 const char *trk_status_string(trk_status s)

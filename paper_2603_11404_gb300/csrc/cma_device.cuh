@@ -456,12 +456,27 @@ __device__ __forceinline__ void cma_tell_impl(const CmaConst &k, CmaState *st, c
         double *t = V; V = V2; V2 = t;
     }
     sandwich64(d, V, S.C, A2, A, tid, nt);  // A = V^T C V
-    // ---- phase 3: one FP64 Jacobi sweep (FP32 angles, FP64-normalised rotations):
-    //      the FP32 pass left off-diagonals at ~1e-6 relative, each rotation
-    //      removes all but ~1e-7 of its entry and the sweep's cross terms are
-    //      second order, so one sweep reaches ~1e-12 relative ----
+    // ---- phase 3: FP64 Jacobi sweeps (FP32 angles, FP64-normalised rotations).
+    //      The FP32 pass left off-diagonals at ~1e-6 relative; each rotation
+    //      removes all but ~1e-7 of its entry, and the cross terms a sweep
+    //      leaves are of order off^2 / gap (quadratic convergence), so one sweep
+    //      usually reaches ~1e-12.  Clustered eigenvalues (small gaps, common
+    //      while C is still near a multiple of I) can leave ~1e-9; a further
+    //      sweep runs while any off-diagonal entry exceeds 1e-11 of the largest
+    //      diagonal one (at most three sweeps in all) ----
     int sweeps64 = 0;
-    for (; sweeps64 < 1; ++sweeps64) {
+    for (; sweeps64 < 3; ++sweeps64) {
+        if (sweeps64 > 0) {
+            double amax = 0.0;
+            for (int i = 0; i < d; ++i) amax = fmax(amax, fabs(A[i * d + i]));
+            const double tol = 1e-11 * amax;
+            int off = 0;
+            for (int e = tid; e < dd; e += nt) {
+                int i = e / d, j = e - i * d;
+                if (j > i && fabs(A[e]) > tol) off = 1;
+            }
+            if (!__syncthreads_or(off)) break;
+        }
         for (int s = 0; s < n2r - 1; ++s) {
             if (tid < np) {
                 int p, q;

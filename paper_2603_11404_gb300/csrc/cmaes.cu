@@ -6,12 +6,11 @@
 
 namespace trk {
 
-__global__ void k_cma_reset(const CmaConst *__restrict__ kp, CmaState *st, const double *mean_dev, int from_est,
-                            const float *joint_reading, int n_inst)
+__device__ void cma_reset_body(const CmaConst &k, CmaState *st, const double *mean_dev, int from_est,
+                               const float *joint_reading, int n_inst, int tid, int nt)
 {
-    const CmaConst &k = *kp;
-    const int d = k.d, tid = threadIdx.x;
-    for (int i = tid; i < d; i += blockDim.x) {
+    const int d = k.d;
+    for (int i = tid; i < d; i += nt) {
         double mi = from_est ? st->est[i] : mean_dev[i];
         int b = i / 9, r = i - 9 * b;
         if (joint_reading && r >= 6 && b < n_inst)
@@ -24,7 +23,7 @@ __global__ void k_cma_reset(const CmaConst *__restrict__ kp, CmaState *st, const
         st->ev[i] = 1.0;
         st->best_x[i] = 0.0f;
     }
-    for (int e = tid; e < d * d; e += blockDim.x) {
+    for (int e = tid; e < d * d; e += nt) {
         double v = (e / d == e % d) ? 1.0 : 0.0;
         st->C[e] = v;
         st->B[e] = v;
@@ -41,6 +40,12 @@ __global__ void k_cma_reset(const CmaConst *__restrict__ kp, CmaState *st, const
         st->jacobi_sweeps = 0;
         st->warn = 0;
     }
+}
+
+__global__ void k_cma_reset(const CmaConst *__restrict__ kp, CmaState *st, const double *mean_dev, int from_est,
+                            const float *joint_reading, int n_inst)
+{
+    cma_reset_body(*kp, st, mean_dev, from_est, joint_reading, n_inst, threadIdx.x, blockDim.x);
 }
 
 __global__ void k_cma_ask(const CmaConst *__restrict__ kp, CmaState *st, double *y, double *z_keep,
@@ -62,6 +67,39 @@ __global__ void __launch_bounds__(kTellThreads) k_cma_tell(const CmaConst *__res
 __global__ void k_cma_finish(const CmaConst *__restrict__ kp, CmaState *st, float *pose_out)
 {
     cma_finish_frame(*kp, st, pose_out, threadIdx.x, blockDim.x);
+}
+
+// Batched forms: block i serves instance i of a batch (tables of device pointers).
+__global__ void k_cma_reset_batch(const CmaConst *const *kp, CmaState *const *st, const int *n_inst)
+{
+    const int i = blockIdx.x;
+    cma_reset_body(*kp[i], st[i], nullptr, 1, nullptr, n_inst[i], threadIdx.x, blockDim.x);
+}
+
+__global__ void __launch_bounds__(kTellThreads) k_cma_tell_batch(const CmaConst *const *kp, CmaState *const *st,
+                                                                 const double *const *y, const float *const *params,
+                                                                 const float *const *loss)
+{
+    __shared__ TellSmem S;
+    const int i = blockIdx.x;
+    cma_tell_block(*kp[i], st[i], y[i], params[i], loss[i], S, threadIdx.x, blockDim.x);
+}
+
+__global__ void k_cma_finish_batch(const CmaConst *const *kp, CmaState *const *st, float *const *pose_out)
+{
+    const int i = blockIdx.x;
+    cma_finish_frame(*kp[i], st[i], pose_out[i], threadIdx.x, blockDim.x);
+}
+
+cudaError_t launch_cma_batch(int op, int n, const CmaConst *const *kp, CmaState *const *st, const int *n_inst,
+                             const double *const *y, const float *const *params, const float *const *loss,
+                             float *const *pose_out, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    if (op == 0) k_cma_reset_batch<<<n, 128, 0, s>>>(kp, st, n_inst);
+    if (op == 1) k_cma_tell_batch<<<n, kTellThreads, 0, s>>>(kp, st, y, params, loss);
+    if (op == 2) k_cma_finish_batch<<<n, 32, 0, s>>>(kp, st, pose_out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_cma_reset(const CmaConst *k, CmaState *st, const double *mean_dev, bool from_est,

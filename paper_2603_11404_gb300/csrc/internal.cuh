@@ -38,8 +38,9 @@ struct CamDev {
     float2 fx_df, fy_df;
 };
 
-// Everything one fitness launch needs.
-struct EvalArgs {
+// Everything one fitness launch needs (a multiple of 16 bytes: batched
+// launches copy it into shared memory in 16-byte pieces).
+struct __align__(16) EvalArgs {
     ChainDev ch;
     CamDev cam;
     const float4 *verts;   // [V] x, y, z, frame index (exact small float)
@@ -115,6 +116,10 @@ __host__ __device__ inline float2 split_df(double x)
 
 cudaError_t launch_eval(const EvalArgs &a, const LaunchCfg &cfg, cudaStream_t s);
 size_t tell_smem_bytes();
+cudaError_t launch_eval_batch(const EvalArgs *descs_dev, const uint32_t *const *masks_dev, const int2 *items_dev,
+                              int n_items, unsigned *next_item_dev, const LaunchCfg &cfg, int n_clusters,
+                              cudaStream_t s);
+cudaError_t prepare_eval_batch(size_t smem, int cluster, int threads, int *max_clusters);
 cudaError_t launch_pack_mask(const uint8_t *mask, uint32_t *packed, int W, int H, int Wq, cudaStream_t s);
 size_t eval_smem_bytes(const EvalArgs &a);
 cudaError_t prepare_eval(size_t smem);
@@ -128,5 +133,43 @@ cudaError_t launch_cma_ask(const CmaConst *k, int lam, CmaState *st, double *y, 
 cudaError_t launch_cma_tell(const CmaConst *k, CmaState *st, const double *y, const float *params,
                             const float *loss, cudaStream_t s);
 cudaError_t launch_cma_finish_frame(const CmaConst *k, CmaState *st, float *pose_out, cudaStream_t s);
+// op 0 reset from the estimate, 1 update, 2 frame epilogue; one block per instance
+cudaError_t launch_cma_batch(int op, int n, const CmaConst *const *kp, CmaState *const *st, const int *n_inst,
+                             const double *const *y, const float *const *params, const float *const *loss,
+                             float *const *pose_out, cudaStream_t s);
 
 }  // namespace trk
+
+// Objects behind the opaque handles of the C ABI.
+struct trk_tracker {
+    int device = 0;
+    trk::ChainDev ch{};
+    trk::CamDev cam{};
+    trk_config cfg{};
+    int V = 0, T = 0, d = 0;
+    float4 *verts = nullptr;
+    int4 *tris = nullptr;
+    int2 *snap = nullptr;       // scratch [lambda_max * n_inst * V]
+    uint32_t *zero_mask = nullptr;
+    trk::LaunchCfg lc{};
+};
+
+struct trk_cmaes {
+    trk_tracker *t = nullptr;
+    trk::CmaConst hk{};
+    trk::CmaConst *k = nullptr;      // device copy
+    trk::CmaState *st = nullptr;
+    double *y = nullptr;        // [lam*d]
+    double *z = nullptr;        // [lam*d] normals of the last population
+    float *params = nullptr;    // [lam*d]
+    float *loss = nullptr;      // [lam]
+    double *mean0 = nullptr;    // [d] creation mean (physical)
+    uint8_t *mask_bytes = nullptr;
+    uint32_t *mask_packed = nullptr;
+    float *joint = nullptr;     // [3*n_inst]
+    float *pose = nullptr;      // [d]
+    unsigned *done = nullptr;   // CTA ticket counter of the fused generation kernel
+    int lam = 0, d = 0;
+};
+
+

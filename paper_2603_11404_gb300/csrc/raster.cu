@@ -388,12 +388,16 @@ __device__ __forceinline__ int2 project_vertex(float4 p, const float *Mh, const 
 // ----------------------------------------------------------------------------
 // The fused fitness kernel.
 // ----------------------------------------------------------------------------
-__global__ void __launch_bounds__(256, 4) k_eval(EvalArgs a)
+// One candidate c of one evaluation (all CTAs of the cluster call it together).
+// mask_override replaces a.mask when not NULL (batched launches); fused_tell
+// lets the last CTA of the launch run the CMA-ES update (single-instance mode).
+__device__ __forceinline__ void eval_candidate(const EvalArgs &a, int c, const uint32_t *mask_override,
+                                               bool fused_tell)
 {
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const int K = (int)cluster.num_blocks();
-    const int c = blockIdx.y;  // candidate
+    const uint32_t *maskp = mask_override ? mask_override : a.mask;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
     const int nI = a.ch.n_inst, nF = a.ch.n_frames;
@@ -541,7 +545,7 @@ __global__ void __launch_bounds__(256, 4) k_eval(EvalArgs a)
         uint32_t part[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) part[q] = (q < K) ? rbm[q][w] : 0u;
-        uint32_t M = a.mask[w];
+        uint32_t M = maskp[w];
         uint32_t S = 0u;
 #pragma unroll
         for (int q = 0; q < 8; ++q) S |= part[q];
@@ -591,7 +595,7 @@ __global__ void __launch_bounds__(256, 4) k_eval(EvalArgs a)
             a.loss[c] = L;
         }
     }
-    if (a.cma_st) {  // the last CTA to finish updates the search distribution
+    if (a.cma_st && fused_tell) {  // the last CTA to finish updates the search distribution
         if (tid == 0) {
             __threadfence();
             unsigned ticket = atomicAdd(a.cma_done, 1u);
@@ -607,6 +611,76 @@ __global__ void __launch_bounds__(256, 4) k_eval(EvalArgs a)
             if (tid == 0) *a.cma_done = 0u;
         }
     }
+}
+
+__global__ void __launch_bounds__(256, 4) k_eval(EvalArgs a) { eval_candidate(a, blockIdx.y, nullptr, true); }
+
+// Persistent batched evaluation: a fixed grid of clusters pulls (instance,
+// candidate) items from a queue (largest first) until it is empty.  CTA 0 of
+// each cluster takes the ticket and the others read it through DSMEM, so the
+// cluster stays in lockstep.  The CMA-ES update runs in a separate launch.
+__global__ void __launch_bounds__(256, 3) k_eval_batch(const EvalArgs *descs, const uint32_t *const *masks,
+                                                       const int2 *items, int n_items, unsigned *next_item)
+{
+    cg::cluster_group cluster = cg::this_cluster();
+    __shared__ int s_item;
+    __shared__ __align__(16) EvalArgs s_args;  // this item's descriptor, read from shared memory
+    for (;;) {
+        if (cluster.block_rank() == 0 && threadIdx.x == 0) s_item = (int)atomicAdd(next_item, 1u);
+        cluster.sync();
+        const int it = *cluster.map_shared_rank(&s_item, 0);
+        cluster.sync();  // every CTA has its ticket before CTA 0 takes the next
+        if (it >= n_items) break;
+        const int2 ic = items[it];
+        const int4 *src = reinterpret_cast<const int4 *>(descs + ic.x);
+        int4 *dst = reinterpret_cast<int4 *>(&s_args);
+        for (int i = threadIdx.x; i < (int)(sizeof(EvalArgs) / 16); i += blockDim.x) dst[i] = src[i];
+        __syncthreads();
+        eval_candidate(s_args, ic.y, masks ? masks[ic.x] : nullptr, false);
+    }
+}
+
+cudaError_t launch_eval_batch(const EvalArgs *descs_dev, const uint32_t *const *masks_dev, const int2 *items_dev,
+                              int n_items, unsigned *next_item_dev, const LaunchCfg &cfg, int n_clusters,
+                              cudaStream_t s)
+{
+    if (n_items == 0) return cudaSuccess;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(cfg.cluster, n_clusters, 1);
+    lc.blockDim = dim3(cfg.threads, 1, 1);
+    lc.dynamicSmemBytes = cfg.smem;
+    lc.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cfg.cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    return cudaLaunchKernelEx(&lc, k_eval_batch, descs_dev, masks_dev, items_dev, n_items, next_item_dev);
+}
+
+cudaError_t prepare_eval_batch(size_t smem, int cluster, int threads, int *max_clusters)
+{
+    static size_t set_to = 0;
+    cudaError_t e = cudaSuccess;
+    if (smem > set_to) {
+        e = cudaFuncSetAttribute(k_eval_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        set_to = smem;
+    }
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(cluster, 1, 1);
+    lc.blockDim = dim3(threads, 1, 1);
+    lc.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    return cudaOccupancyMaxActiveClusters(max_clusters, k_eval_batch, &lc);
 }
 
 size_t tell_smem_bytes() { return sizeof(TellSmem); }

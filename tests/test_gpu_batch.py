@@ -1,0 +1,81 @@
+"""Heterogeneous batches: one persistent launch per generation over instances of
+different image sizes, meshes, instrument counts and population sizes gives
+exactly the per-instance results."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_11404_gb300 import workload as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_11404_gb300 import build
+    build.build()
+    from paper_2603_11404_gb300 import api as a
+    return a
+
+
+def _instances(api):
+    specs = [
+        ("c1", "c1", 1, wl.LOSS_XOR, 16, None),
+        ("c2", "c2", 1, wl.LOSS_ONE_MINUS_IOU, 64, None),
+        ("c1", "c1", 2, wl.LOSS_ONE_MINUS_IOU, 32, wl.Intrinsics(150.0, 150.0, 50.0, 38.5, 101, 77)),
+        ("5000", "c2", 1, wl.LOSS_MSE_APP, 48, wl.Intrinsics(400.0, 400.0, 160.0, 128.0, 320, 256)),
+    ]
+    out = []
+    for k, (mesh, cam, ni, loss, lam, K) in enumerate(specs):
+        sc = wl.make_scene(mesh, cam, n_instruments=ni, K=K)
+        rng = np.random.default_rng(300 + k)
+        gt = np.concatenate([wl.sample_state(rng, sc.K) for _ in range(ni)])
+        M = wl.corrupt_mask(oracle.render(sc, gt), rng)
+        tr = api.Tracker(sc, loss_kind=loss, lambda_max=lam, lambda_app=0.25)
+        Mp = tr.pack_mask(torch.from_numpy(M).cuda())
+        out.append(dict(sc=sc, gt=gt, tr=tr, Mp=Mp, lam=lam, rng=rng))
+    return out
+
+
+def test_batch_eval_matches_single(api):
+    inst = _instances(api)
+    P = [torch.from_numpy(wl.population_around(x["rng"], x["gt"], x["lam"])).cuda() for x in inst]
+    b = api.Batch([x["tr"] for x in inst], lams=[x["lam"] for x in inst])
+    for shape in [(8, 256), (4, 128), (1, 256)]:
+        b.set_launch(*shape)
+        losses, counts = b.eval(P, [x["Mp"] for x in inst])
+        torch.cuda.synchronize()
+        for x, p, l, c in zip(inst, P, losses, counts):
+            rl, rc = x["tr"].eval_population(p, x["Mp"], counts=True)
+            assert torch.equal(c, rc), shape
+            assert torch.equal(l.view(torch.int32), rl.view(torch.int32)), shape
+    c, t, us = b.autotune([x["Mp"] for x in inst], params=P, reps=3)
+    assert c in (1, 2, 4, 8) and t in (128, 256) and us > 0
+    assert b.launch()[:2] == (c, t)
+    losses, counts = b.eval(P, [x["Mp"] for x in inst])
+    for x, p, cc in zip(inst, P, counts):
+        assert torch.equal(cc, x["tr"].eval_population(p, x["Mp"], counts=True)[1])
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_batch_track_frame_matches_single(api, use_graph):
+    inst = _instances(api)
+    scales = lambda x: wl.default_scales(x["sc"].d)
+    opt_b = [api.CMAES(x["tr"], x["lam"], x["gt"] + 0.01, scales(x), seed=10 + i, block_diag=x["sc"].d == 18)
+             for i, x in enumerate(inst)]
+    opt_s = [api.CMAES(x["tr"], x["lam"], x["gt"] + 0.01, scales(x), seed=10 + i, block_diag=x["sc"].d == 18)
+             for i, x in enumerate(inst)]
+    b = api.Batch([x["tr"] for x in inst], optimisers=opt_b)
+    for frame in range(3):
+        poses = b.track_frame([x["Mp"] for x in inst], 4, use_graph=use_graph)
+        torch.cuda.synchronize()
+        for x, o, pb in zip(inst, opt_s, poses):
+            ps = o.track_frame(x["Mp"], 4)
+            torch.cuda.synchronize()
+            assert torch.equal(pb, ps), frame
+    for ob, os_ in zip(opt_b, opt_s):
+        sa, sb = ob.state(), os_.state()
+        assert np.array_equal(sa["C"], sb["C"]) and sa["sigma"] == sb["sigma"]
