@@ -43,7 +43,7 @@ ALGO_OPS_PER_VERT, ALGO_OPS_PER_TRI, ALGO_OPS_PER_BBOX_PX = 16, 40, 4
 # ncu (profiles/k_eval_640x512.md), valid for the kernel sources with this digest;
 # reported as null once those sources change.
 KEVAL_TRAFFIC_BYTES = 614656
-KEVAL_TRAFFIC_DIGEST = None  # filled in when the capture is committed
+KEVAL_TRAFFIC_DIGEST = "6ddbecfd81d2b5a6"
 KERNEL_SOURCES = ("raster.cu", "cma_device.cuh", "df.cuh", "internal.cuh")
 
 
@@ -64,6 +64,8 @@ def _args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-forms", action="store_true", help="skip the batching and serving measurements")
+    p.add_argument("--serve-frames", type=int, default=300, help="frames per camera stream in the serving run")
     p.add_argument("--profile-target", action="store_true",
                    help="run a short fixed launch sequence for ncu (2 warm-up + 3 plain k_eval launches at "
                         "640x512, lambda = 64, then 3 fused generations) and exit")
@@ -273,19 +275,218 @@ def run_ours(a):
                        "e2e_p50": float(np.percentile(e2e_ms, 50)), "e2e_p99": float(np.percentile(e2e_ms, 99))},
         "e2e": {"value": evals / e2e_total, "unit": UNIT, "h2d_bytes_per_step": H * W,
                 "d2h_bytes_per_step": 9 * 4 + 4},
-        "gpu_launches": a.steps * (2 + 3 * GENS),
+        "gpu_launches": a.steps * (1 + GENS),  # per frame: reset + GENS fused generation launches
         "roofline": roofline,
         "tracking_error": {"rot_rad_median": float(np.median(pose_err[:, :3])),
                            "trans_mm_median": float(np.median(pose_err[:, 3:6])),
                            "joint_median": float(np.median(pose_err[:, 6:]))},
         "clocks": clk.summary(),
     }
+    if not a.no_forms:
+        out["batching"] = bench_batching(a, rank)
+        out["serving"] = bench_serving(a, rank)
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(a.cpu_seconds)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def _masks_for(api, tr, sc, traj, rng):
+    import torch
+    out = []
+    for st in traj:
+        S = api.unpack_mask(tr.render(torch.from_numpy(st.astype(np.float32)).cuda()), sc.K.width).cpu().numpy()
+        out.append(wl.corrupt_mask(S, rng))
+    return out
+
+
+BATCH_IMAGES = [(320, 256), (640, 512), (960, 768), (1280, 1024)]
+BATCH_LAMS = [32, 64, 128, 256]
+BATCH_MESHES = ["5000", "10000", "20000", "40000"]
+
+
+def batching_instances(n: int = 24):
+    """The heterogeneous batch: instance k has image BATCH_IMAGES[k % 4] (focal
+    length 1.25 x width), population BATCH_LAMS[(k // 4) % 4], mesh
+    BATCH_MESHES[(k + k // 4) % 4] triangles, two instruments when k % 3 == 0."""
+    out = []
+    for k in range(n):
+        W, H = BATCH_IMAGES[k % 4]
+        K = wl.Intrinsics(1.25 * W, 1.25 * W, W / 2, H / 2, W, H)
+        out.append(dict(K=K, lam=BATCH_LAMS[(k // 4) % 4], mesh=BATCH_MESHES[(k + k // 4) % 4],
+                        n_inst=2 if k % 3 == 0 else 1))
+    return out
+
+
+def bench_batching(a, rank, n_frames: int = 6):
+    """Form (2): 24 uneven instances tracked together -- one persistent fitness
+    launch per generation, replayed as a CUDA graph, launch shape from the
+    autotuner -- against the plain form (track_frame_device per instance, one
+    after the other) on the same frames.  Both give bit-identical poses."""
+    import torch
+
+    from paper_2603_11404_gb300 import api
+    rng = np.random.default_rng(SEED + 31 + 7919 * rank)
+    inst = []
+    for k, spec in enumerate(batching_instances()):
+        sc = wl.make_scene(spec["mesh"], "c2", n_instruments=spec["n_inst"], K=spec["K"])
+        p0 = np.concatenate([wl.sample_state(rng, sc.K) for _ in range(spec["n_inst"])])
+        traj = wl.sinusoidal_trajectory(rng, p0, n_frames + 1)
+        tr = api.Tracker(sc, loss_kind=wl.LOSS_ONE_MINUS_IOU, lambda_max=spec["lam"])
+        masks = [tr.pack_mask(torch.from_numpy(m).cuda()) for m in _masks_for(api, tr, sc, traj, rng)]
+        inst.append(dict(sc=sc, tr=tr, p0=p0, lam=spec["lam"], masks=masks))
+
+    def optimisers(seed):
+        return [api.CMAES(x["tr"], x["lam"], x["p0"], wl.default_scales(x["sc"].d), sigma0=1.0, seed=seed + i,
+                          block_diag=x["sc"].d == 18) for i, x in enumerate(inst)]
+
+    evals_per_frame = sum(x["lam"] for x in inst) * GENS
+    opt_b = optimisers(SEED + 500)
+    b = api.Batch([x["tr"] for x in inst], optimisers=opt_b)
+    c, t, us = b.autotune([x["masks"][0] for x in inst], reps=3)
+    poses = [torch.empty(x["sc"].d, dtype=torch.float32, device="cuda") for x in inst]
+    b.track_frame([x["masks"][0] for x in inst], GENS, poses=poses)  # warm-up: records the graph
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_frames)]
+    stream = torch.cuda.current_stream()
+    for f in range(n_frames):
+        ev[f][0].record(stream)
+        b.track_frame([x["masks"][f + 1] for x in inst], GENS, poses=poses, stream=stream)
+        ev[f][1].record(stream)
+    torch.cuda.synchronize()
+    bms = np.array([s_.elapsed_time(e_) for s_, e_ in ev])
+    opt_p = optimisers(SEED + 500)
+    for o, x, p in zip(opt_p, inst, poses):
+        o.track_frame(x["masks"][0], GENS, pose_out=p)
+    torch.cuda.synchronize()
+    pms = []
+    for f in range(n_frames):
+        s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s_.record(stream)
+        for o, x, p in zip(opt_p, inst, poses):
+            o.track_frame(x["masks"][f + 1], GENS, pose_out=p)
+        e_.record(stream)
+        torch.cuda.synchronize()
+        pms.append(s_.elapsed_time(e_))
+    pms = np.array(pms)
+    return {"workload": "24 instances: images 320x256..1280x1024, lambda in {32,64,128,256}, meshes 5k-40k "
+                        "triangles, every third bi-manual (d=18); %d frames, %d generations, loss 1-IoU" % (n_frames, GENS),
+            "triangles": [int(x["sc"].n_tris) for x in inst],
+            "evals_per_frame": evals_per_frame,
+            "batched": {"evals_per_s": evals_per_frame / (bms.mean() / 1e3), "frame_ms_p50": float(np.median(bms)),
+                        "frame_ms_max": float(bms.max()), "launch": {"cluster": c, "threads": t, "autotune_us": us},
+                        "cuda_graph": True},
+            "plain": {"evals_per_s": evals_per_frame / (pms.mean() / 1e3), "frame_ms_p50": float(np.median(pms)),
+                      "frame_ms_max": float(pms.max())},
+            "speedup": float(pms.mean() / bms.mean()),
+            "results": "bit-identical poses (tests/test_gpu_batch.py)"}
+
+
+SERVE_STREAMS = 8
+SERVE_CYCLE = 30  # distinct frames per stream; longer runs replay them in order
+
+
+def bench_serving(a, rank):
+    """Form (5): 8 camera streams, Poisson arrivals at 30 Hz each, half
+    joint-angle-free single-instrument (d=9, no joint readings), half bi-manual
+    (d=18) with joint readings; 640x512 masks, lambda = 64, 5 generations.
+    Served with continuous batching, then by the plain form (one
+    track_frame_host per frame in arrival order) on the same arrivals, then
+    both saturated (every frame submitted at once)."""
+    import torch
+
+    from paper_2603_11404_gb300 import api
+    rng = np.random.default_rng(SEED + 77 + 7919 * rank)
+    n_per = a.serve_frames
+    streams = []
+    for k in range(SERVE_STREAMS):
+        bim = k % 2 == 1
+        sc = wl.make_scene("c2", "c2", n_instruments=2 if bim else 1)
+        p0 = np.concatenate([wl.sample_state(rng, sc.K) for _ in range(sc.n_instruments)])
+        traj = wl.sinusoidal_trajectory(rng, p0, SERVE_CYCLE)
+        tr = api.Tracker(sc, loss_kind=wl.LOSS_ONE_MINUS_IOU, lambda_max=LAM)
+        masks = _masks_for(api, tr, sc, traj, rng)
+        joints = [np.concatenate([st[b * 9 + 6: b * 9 + 9] for b in range(sc.n_instruments)]).astype(np.float32)
+                  + rng.normal(size=3 * sc.n_instruments).astype(np.float32) * 0.02 for st in traj]
+        streams.append(dict(sc=sc, tr=tr, p0=p0, masks=masks, joints=joints if bim else None, bim=bim))
+    arrivals = []  # (t, stream, frame)
+    for k in range(SERVE_STREAMS):
+        t = 0.0
+        for f in range(n_per):
+            t += rng.exponential(1 / 30.0)
+            arrivals.append((t, k, f))
+    arrivals.sort()
+
+    def optimiser(x, k):
+        return api.CMAES(x["tr"], LAM, x["p0"], wl.default_scales(x["sc"].d), sigma0=1.0, seed=SEED + 900 + k,
+                         block_diag=x["bim"])
+
+    def frame(k, f):
+        x = streams[k]
+        return x["masks"][f % SERVE_CYCLE], (x["joints"][f % SERVE_CYCLE] if x["bim"] else None)
+
+    def served(realtime: bool):
+        srv = api.Server(max_active=SERVE_STREAMS, max_streams=SERVE_STREAMS, max_pending=64,
+                         max_pixels=640 * 512, max_lambda=LAM)
+        sids = [srv.add_stream(optimiser(x, k), GENS, use_joint_reading=x["bim"]) for k, x in enumerate(streams)]
+        # warm-up: one frame per stream
+        for k in range(SERVE_STREAMS):
+            m, j = frame(k, 0)
+            srv.submit(sids[k], m, j, tag=1 << 40)
+        srv.run_until_idle()
+        res, i = [], 0
+        t0 = api.Server.now() + 0.05
+        while len(res) < len(arrivals):
+            now = api.Server.now()
+            while i < len(arrivals) and (not realtime or t0 + arrivals[i][0] <= now):
+                t, k, f = arrivals[i]
+                m, j = frame(k, f)
+                if not srv.submit(sids[k], m, j, tag=f, t_submit=(t0 + t) if realtime else -1.0):
+                    break  # staging pool full: step first (a real-time frame keeps its arrival time)
+                i += 1
+            act, q = srv.step()
+            res += srv.poll()
+            if act == 0 and q == 0:
+                res += srv.poll(wait=True)
+                if i < len(arrivals):
+                    time.sleep(max(0.0, t0 + arrivals[i][0] - api.Server.now()))
+        lat = np.array([r["t_done"] - r["t_submit"] for r in res]) * 1e3
+        span = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
+        return {"frames": len(res), "frames_per_s": len(res) / span, "latency_ms_p50": float(np.percentile(lat, 50)),
+                "latency_ms_p99": float(np.percentile(lat, 99)), "ticks": srv.stats()["ticks"]}
+
+    def plain(realtime: bool):
+        opts = [optimiser(x, k) for k, x in enumerate(streams)]
+        for k, o in enumerate(opts):
+            m, j = frame(k, 0)
+            o.track_frame_host(m, GENS, j)
+        lat = []
+        t0 = time.perf_counter() + 0.05
+        first = None
+        for t, k, f in arrivals:
+            if realtime:
+                while time.perf_counter() < t0 + t:
+                    time.sleep(max(0.0, min(0.001, t0 + t - time.perf_counter())))
+            arr = t0 + t if realtime else time.perf_counter()
+            first = arr if first is None else first
+            m, j = frame(k, f)
+            opts[k].track_frame_host(m, GENS, j)
+            lat.append(time.perf_counter() - arr)
+        span = time.perf_counter() - first
+        lat = np.array(lat) * 1e3
+        return {"frames": len(lat), "frames_per_s": len(lat) / span, "latency_ms_p50": float(np.percentile(lat, 50)),
+                "latency_ms_p99": float(np.percentile(lat, 99))}
+
+    return {"workload": "%d streams (4 joint-free d=9, 4 bi-manual d=18 with joint readings), 640x512, "
+                        "20k-triangle meshes, lambda=64, %d generations, Poisson 30 Hz per stream, %d frames "
+                        "per stream (masks cycle through %d frames)" % (SERVE_STREAMS, GENS, n_per, SERVE_CYCLE),
+            "served_realtime": served(True), "plain_realtime": plain(True),
+            "served_saturated": served(False), "plain_saturated": plain(False),
+            "latency": "t_done - arrival; t_done = device completion of the frame's last tick (pose download "
+                       "included) for the server, host return of track_frame_host for the plain form",
+            "results": "bit-identical poses alone, in the mix and in the plain form (tests/test_gpu_serve.py)"}
 
 
 def _algo_ops(sc, snap):

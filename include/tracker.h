@@ -336,6 +336,84 @@ trk_status batch_track_frame(trk_batch *b, const uint32_t *const *masks_dev, int
 trk_status batch_autotune(trk_batch *b, const float *const *params_dev, const uint32_t *const *masks_dev,
                           int32_t reps, int32_t *cluster_out, int32_t *threads_out, float *us_out, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Serving: frames from several camera streams with continuous batching.  Not
+ * a paper feature: the paper tracks one video stream per process.  Each camera
+ * stream keeps its CMA-ES state (an optimiser from cmaes_create) resident on
+ * the device and warm-starts it frame to frame.  Submitted frames wait on the
+ * host; server_step admits waiting frames into free slots (one frame per
+ * stream at a time, at most max_active in all) and enqueues one *tick*: one
+ * CMA-ES generation of every admitted frame, their candidates evaluated
+ * together in one persistent launch and their updates in one launch.  A frame
+ * finishes after its stream's `generations` ticks; frames admitted later join
+ * at the next tick.  Every frame is computed by the kernels of
+ * track_frame_device, so its pose is bit-identical to tracking it alone.
+ * The server owns one CUDA stream; its calls are not thread-safe.
+ * ------------------------------------------------------------------------- */
+typedef struct trk_server trk_server;
+
+/* A finished frame.  Times are seconds on the clock of server_now(); t_done
+ * is the device completion time of the frame's last tick (its pose download
+ * included), mapped onto that clock. */
+typedef struct {
+    uint64_t tag;                /* the caller's tag from server_submit           */
+    double t_submit, t_admit, t_done;
+    int32_t stream, d;
+    float pose[TRK_MAX_D];       /* the frame's estimate, d entries                */
+    float best_loss;
+    int32_t pad;
+} trk_frame_result;
+
+/* Monotonic host clock (seconds) used for all server times. */
+double server_now(void);
+
+/* max_active: frames in slots at once; max_streams: camera streams that can
+ * be open; max_pending: frames submitted but not yet admitted, over all
+ * streams (each holds a pinned staging copy of max_pixels bytes); max_lambda:
+ * largest population of a stream; hbm_reserve_bytes: device memory that
+ * server_add_stream must leave free; cluster / threads: launch shape of the
+ * fitness launch (0 = 8 CTAs x 256 threads).  Synchronous. */
+trk_status server_create(int32_t max_active, int32_t max_streams, int32_t max_pending, int64_t max_pixels,
+                         int32_t max_lambda, int64_t hbm_reserve_bytes, int32_t cluster, int32_t threads,
+                         trk_server **out);
+trk_status server_destroy(trk_server *v);
+
+/* Open a camera stream served by optimiser es (its tracker's image must have
+ * at most max_pixels pixels); each frame runs `generations` generations; with
+ * use_joint_reading != 0 every submitted frame carries joint readings that
+ * reset the joint coordinates of the mean.  Admission by device memory: the
+ * stream's raster scratch (lam * n_instruments * n_verts * 8 bytes) is
+ * allocated only if hbm_reserve_bytes stay free; otherwise TRK_EBUSY.
+ * Synchronous.  *stream_id receives the stream's index. */
+trk_status server_add_stream(trk_server *v, trk_cmaes *es, int32_t generations, int32_t use_joint_reading,
+                             int32_t *stream_id);
+/* Close an idle stream (TRK_EBUSY while it has frames queued or in flight). */
+trk_status server_remove_stream(trk_server *v, int32_t stream_id);
+
+/* Queue a frame: copies mask_host [H*W] bytes (0/1) and, for streams opened
+ * with joint readings, joint_reading_host [3*n_instruments] into a staging
+ * buffer before returning.  t_submit < 0 stamps server_now().  TRK_EBUSY when
+ * max_pending frames are already waiting. */
+trk_status server_submit(trk_server *v, int32_t stream_id, const uint8_t *mask_host, const float *joint_reading_host,
+                         uint64_t tag, double t_submit);
+
+/* Admit waiting frames into free slots and enqueue one tick for every frame
+ * in a slot (no-op when none).  Never waits for the device: while two ticks
+ * are still running it enqueues nothing, so a newly admitted frame waits for
+ * at most one tick; callers loop over server_step / server_poll.
+ * n_active_out / n_queued_out (may be NULL): frames in slots, frames still
+ * waiting. */
+trk_status server_step(trk_server *v, int32_t *n_active_out, int32_t *n_queued_out);
+
+/* Move up to max_out finished frames, in completion order, into out; with
+ * wait != 0 first waits for every enqueued tick. */
+trk_status server_poll(trk_server *v, trk_frame_result *out, int32_t max_out, int32_t wait, int32_t *n_out);
+
+/* Counters: ticks enqueued so far, frames in slots, frames waiting, free
+ * staging buffers (any output may be NULL). */
+trk_status server_stats(const trk_server *v, int64_t *ticks, int32_t *n_active, int32_t *n_queued,
+                        int32_t *free_staging);
+
 /* Checkpoint: the whole optimiser state as a plain blob.  cmaes_save with
  * blob = NULL sets *n to the size needed.  A loaded optimiser continues
  * bit-identically.  Both synchronise the stream. */

@@ -51,6 +51,12 @@ class Config(C.Structure):
                 ("lambda_max", C.c_int32), ("cluster", C.c_int32), ("block_threads", C.c_int32)]
 
 
+class FrameResult(C.Structure):
+    _fields_ = [("tag", C.c_uint64), ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
+                ("stream", C.c_int32), ("d", C.c_int32), ("pose", C.c_float * TRK_MAX_D), ("best_loss", C.c_float),
+                ("pad", C.c_int32)]
+
+
 P = C.c_void_p
 I32 = C.c_int32
 # name -> argtypes (every function returns trk_status = int)
@@ -85,6 +91,14 @@ SIGNATURES = {
     "batch_eval": [P, P, P, P, P, P],
     "batch_track_frame": [P, P, I32, P, I32, P],
     "batch_autotune": [P, P, P, I32, P, P, P, P],
+    "server_create": [I32, I32, I32, C.c_int64, I32, C.c_int64, I32, I32, P],
+    "server_destroy": [P],
+    "server_add_stream": [P, P, I32, I32, P],
+    "server_remove_stream": [P, I32],
+    "server_submit": [P, I32, P, P, C.c_uint64, C.c_double],
+    "server_step": [P, P, P],
+    "server_poll": [P, P, I32, I32, P],
+    "server_stats": [P, P, P, P, P],
 }
 
 _lib = None
@@ -107,6 +121,8 @@ def lib():
             L.trk_status_string.argtypes = [C.c_int]
             L.tracker_last_error.restype = C.c_char_p
             L.tracker_last_error.argtypes = []
+            L.server_now.restype = C.c_double
+            L.server_now.argtypes = []
             _lib = L
     return _lib
 
@@ -124,4 +140,4 @@ def declared_symbols():
     import re
     hdr = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "tracker.h")
     src = open(hdr).read()
-    return sorted(set(re.findall(r"^\s*(?:trk_status|const char \*)\s*(\w+)\s*\(", src, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:trk_status|const char \*|double)\s*(\w+)\s*\(", src, re.M)))

@@ -327,3 +327,91 @@ class Batch:
         call("batch_autotune", self.h, None if params is None else _ptr_array(params), _ptr_array(masks), int(reps),
              C.byref(c), C.byref(t), C.byref(us), _stream(stream))
         return c.value, t.value, us.value
+
+
+class Server:
+    """server_*: camera streams tracked with continuous batching (one CMA-ES
+    generation of every admitted frame per tick)."""
+
+    def __init__(self, max_active: int = 8, max_streams: int = 8, max_pending: int = 64,
+                 max_pixels: int = 640 * 512, max_lambda: int = 256, hbm_reserve_bytes: int = 0,
+                 cluster: int = 0, threads: int = 0):
+        h = C.c_void_p()
+        call("server_create", int(max_active), int(max_streams), int(max_pending), int(max_pixels), int(max_lambda),
+             int(hbm_reserve_bytes), int(cluster), int(threads), C.byref(h))
+        self.h = h
+        self._out = (_abi.FrameResult * 256)()
+        self.optimisers = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            call("server_destroy", self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def now() -> float:
+        return _abi.lib().server_now()
+
+    def add_stream(self, cmaes: "CMAES", generations: int, use_joint_reading: bool = False) -> int:
+        sid = C.c_int32()
+        call("server_add_stream", self.h, cmaes.h, int(generations), int(bool(use_joint_reading)), C.byref(sid))
+        self.optimisers[sid.value] = cmaes
+        return sid.value
+
+    def remove_stream(self, sid: int):
+        call("server_remove_stream", self.h, int(sid))
+        self.optimisers.pop(sid, None)
+
+    def submit(self, sid: int, mask_u8: np.ndarray, joint_reading=None, tag: int = 0, t_submit: float = -1.0):
+        """Queue a frame; returns False (nothing queued) when the staging pool is full."""
+        m = np.ascontiguousarray(mask_u8, np.uint8)
+        j = None if joint_reading is None else np.ascontiguousarray(joint_reading, np.float32)
+        L = _abi.lib()
+        rc = L.server_submit(self.h, int(sid), m.ctypes.data, None if j is None else j.ctypes.data, int(tag),
+                             float(t_submit))
+        if rc == 6:  # TRK_EBUSY
+            return False
+        if rc != 0:
+            raise _abi.TrkError(rc, "server_submit", L.tracker_last_error().decode(errors="replace"))
+        return True
+
+    def step(self):
+        """Enqueue one tick; returns (frames in slots, frames waiting)."""
+        a, q = C.c_int32(), C.c_int32()
+        call("server_step", self.h, C.byref(a), C.byref(q))
+        return a.value, q.value
+
+    def poll(self, wait: bool = False):
+        out, res = [], self._out
+        first = True
+        while True:
+            n = C.c_int32()
+            call("server_poll", self.h, res, len(res), int(bool(wait and first)), C.byref(n))
+            first = False
+            for i in range(n.value):
+                r = res[i]
+                out.append(dict(stream=r.stream, tag=r.tag, t_submit=r.t_submit, t_admit=r.t_admit, t_done=r.t_done,
+                                pose=np.array(r.pose[:r.d], np.float32), best_loss=r.best_loss))
+            if n.value < len(res):
+                return out
+
+    def stats(self):
+        t, a, q, f = C.c_int64(), C.c_int32(), C.c_int32(), C.c_int32()
+        call("server_stats", self.h, C.byref(t), C.byref(a), C.byref(q), C.byref(f))
+        return dict(ticks=t.value, active=a.value, queued=q.value, free_staging=f.value)
+
+    def run_until_idle(self):
+        """Step until every queued frame has finished; returns the results."""
+        out = []
+        while True:
+            a, q = self.step()
+            out += self.poll()
+            if a == 0 and q == 0:
+                break
+        return out + self.poll(wait=True)

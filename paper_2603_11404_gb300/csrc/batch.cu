@@ -37,11 +37,7 @@ struct trk_batch {
     int n_items = 0;
     unsigned *next_item = nullptr;
     int2 *snap = nullptr;               // batch-owned scratch for every instance
-    const CmaConst **t_k = nullptr;
-    CmaState **t_st = nullptr;
-    const double **t_y = nullptr;
-    const float **t_params = nullptr, **t_loss = nullptr;
-    int *t_ninst = nullptr;
+    BatchTables tb;                     // CMA-ES tables (tb.pose aliases poses)
     const void **pin = nullptr;         // pinned staging for the two pointer tables
     LaunchCfg lc{};
     int n_clusters = 0;
@@ -61,12 +57,12 @@ static void batch_free(trk_batch *b)
     cudaFree(b->items);
     cudaFree(b->next_item);
     cudaFree(b->snap);
-    cudaFree(b->t_k);
-    cudaFree(b->t_st);
-    cudaFree(b->t_y);
-    cudaFree(b->t_params);
-    cudaFree(b->t_loss);
-    cudaFree(b->t_ninst);
+    cudaFree(b->tb.k);
+    cudaFree(b->tb.st);
+    cudaFree(b->tb.y);
+    cudaFree(b->tb.params);
+    cudaFree(b->tb.loss);
+    cudaFree(b->tb.ninst);
     cudaFreeHost(b->pin);
     delete b;
 }
@@ -146,12 +142,12 @@ trk_status batch_create(trk_tracker *const *trackers, trk_cmaes *const *optimise
         (e = cudaMalloc(&b->items, sizeof(int2) * b->n_items)) != cudaSuccess ||
         (e = cudaMalloc(&b->next_item, sizeof(unsigned))) != cudaSuccess ||
         (e = cudaMalloc(&b->snap, sizeof(int2) * snap_total)) != cudaSuccess ||
-        (e = cudaMalloc(&b->t_k, sizeof(void *) * n)) != cudaSuccess ||
-        (e = cudaMalloc(&b->t_st, sizeof(void *) * n)) != cudaSuccess ||
-        (e = cudaMalloc(&b->t_y, sizeof(void *) * n)) != cudaSuccess ||
-        (e = cudaMalloc(&b->t_params, sizeof(void *) * n)) != cudaSuccess ||
-        (e = cudaMalloc(&b->t_loss, sizeof(void *) * n)) != cudaSuccess ||
-        (e = cudaMalloc(&b->t_ninst, sizeof(int) * n)) != cudaSuccess ||
+        (e = cudaMalloc(&b->tb.k, sizeof(void *) * n)) != cudaSuccess ||
+        (e = cudaMalloc(&b->tb.st, sizeof(void *) * n)) != cudaSuccess ||
+        (e = cudaMalloc(&b->tb.y, sizeof(void *) * n)) != cudaSuccess ||
+        (e = cudaMalloc(&b->tb.params, sizeof(void *) * n)) != cudaSuccess ||
+        (e = cudaMalloc(&b->tb.loss, sizeof(void *) * n)) != cudaSuccess ||
+        (e = cudaMalloc(&b->tb.ninst, sizeof(int) * n)) != cudaSuccess ||
         (e = cudaMallocHost(&b->pin, sizeof(void *) * 2 * n)) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking)) != cudaSuccess) {
         batch_free(b);
@@ -209,16 +205,17 @@ trk_status batch_create(trk_tracker *const *trackers, trk_cmaes *const *optimise
         for (int c = 0; c < b->lam[i]; ++c) items.push_back(make_int2(i, c));
     if ((e = cudaMemcpy(b->descs, b->hdescs.data(), sizeof(EvalArgs) * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(b->items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(b->t_k, hk.data(), sizeof(void *) * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(b->t_st, hst.data(), sizeof(void *) * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(b->t_y, hy.data(), sizeof(void *) * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(b->t_params, hp.data(), sizeof(void *) * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(b->t_loss, hl.data(), sizeof(void *) * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(b->t_ninst, hni.data(), sizeof(int) * n, cudaMemcpyHostToDevice)) != cudaSuccess) {
+        (e = cudaMemcpy(b->tb.k, hk.data(), sizeof(void *) * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(b->tb.st, hst.data(), sizeof(void *) * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(b->tb.y, hy.data(), sizeof(void *) * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(b->tb.params, hp.data(), sizeof(void *) * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(b->tb.loss, hl.data(), sizeof(void *) * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(b->tb.ninst, hni.data(), sizeof(int) * n, cudaMemcpyHostToDevice)) != cudaSuccess) {
         batch_free(b);
         set_last_error(cudaGetErrorString(e));
         return TRK_ECUDA;
     }
+    b->tb.pose = b->poses;
     trk_status st = batch_configure(b, cluster, threads);
     if (st != TRK_OK) {
         batch_free(b);
@@ -297,16 +294,16 @@ trk_status batch_eval(trk_batch *b, const float *const *params_dev, const uint32
 // reset, generations x (fitness + updates), epilogue: enqueued on s
 static cudaError_t enqueue_frame(trk_batch *b, int generations, cudaStream_t s)
 {
-    cudaError_t e = launch_cma_batch(0, b->n, b->t_k, b->t_st, b->t_ninst, nullptr, nullptr, nullptr, nullptr, s);
+    cudaError_t e = launch_cma_batch(0, b->n, nullptr, b->tb, s);
     for (int g = 0; g < generations && e == cudaSuccess; ++g) {
         if ((e = cudaMemsetAsync(b->next_item, 0, sizeof(unsigned), s)) != cudaSuccess) break;
         if ((e = launch_eval_batch(b->descs, b->masks, b->items, b->n_items, b->next_item, b->lc, b->n_clusters,
                                    s)) != cudaSuccess)
             break;
-        e = launch_cma_batch(1, b->n, b->t_k, b->t_st, b->t_ninst, b->t_y, b->t_params, b->t_loss, nullptr, s);
+        e = launch_cma_batch(1, b->n, nullptr, b->tb, s);
     }
     if (e == cudaSuccess)
-        e = launch_cma_batch(2, b->n, b->t_k, b->t_st, b->t_ninst, nullptr, nullptr, nullptr, b->poses, s);
+        e = launch_cma_batch(2, b->n, nullptr, b->tb, s);
     return e;
 }
 

@@ -69,36 +69,40 @@ __global__ void k_cma_finish(const CmaConst *__restrict__ kp, CmaState *st, floa
     cma_finish_frame(*kp, st, pose_out, threadIdx.x, blockDim.x);
 }
 
-// Batched forms: block i serves instance i of a batch (tables of device pointers).
-__global__ void k_cma_reset_batch(const CmaConst *const *kp, CmaState *const *st, const int *n_inst)
+// Batched forms: block b serves instance sel[b] (or b when sel is NULL) of
+// tables of device pointers indexed by instance.
+__device__ __forceinline__ int batch_instance(const int *sel) { return sel ? sel[blockIdx.x] : (int)blockIdx.x; }
+
+__global__ void k_cma_reset_batch(const int *sel, const CmaConst *const *kp, CmaState *const *st, const int *n_inst,
+                                  const float *const *joint)
 {
-    const int i = blockIdx.x;
-    cma_reset_body(*kp[i], st[i], nullptr, 1, nullptr, n_inst[i], threadIdx.x, blockDim.x);
+    const int i = batch_instance(sel);
+    cma_reset_body(*kp[i], st[i], nullptr, 1, joint ? joint[i] : nullptr, n_inst[i], threadIdx.x, blockDim.x);
 }
 
-__global__ void __launch_bounds__(kTellThreads) k_cma_tell_batch(const CmaConst *const *kp, CmaState *const *st,
-                                                                 const double *const *y, const float *const *params,
+__global__ void __launch_bounds__(kTellThreads) k_cma_tell_batch(const int *sel, const CmaConst *const *kp,
+                                                                 CmaState *const *st, const double *const *y,
+                                                                 const float *const *params,
                                                                  const float *const *loss)
 {
     __shared__ TellSmem S;
-    const int i = blockIdx.x;
+    const int i = batch_instance(sel);
     cma_tell_block(*kp[i], st[i], y[i], params[i], loss[i], S, threadIdx.x, blockDim.x);
 }
 
-__global__ void k_cma_finish_batch(const CmaConst *const *kp, CmaState *const *st, float *const *pose_out)
+__global__ void k_cma_finish_batch(const int *sel, const CmaConst *const *kp, CmaState *const *st,
+                                   float *const *pose_out)
 {
-    const int i = blockIdx.x;
+    const int i = batch_instance(sel);
     cma_finish_frame(*kp[i], st[i], pose_out[i], threadIdx.x, blockDim.x);
 }
 
-cudaError_t launch_cma_batch(int op, int n, const CmaConst *const *kp, CmaState *const *st, const int *n_inst,
-                             const double *const *y, const float *const *params, const float *const *loss,
-                             float *const *pose_out, cudaStream_t s)
+cudaError_t launch_cma_batch(int op, int n, const int *sel, const BatchTables &t, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
-    if (op == 0) k_cma_reset_batch<<<n, 128, 0, s>>>(kp, st, n_inst);
-    if (op == 1) k_cma_tell_batch<<<n, kTellThreads, 0, s>>>(kp, st, y, params, loss);
-    if (op == 2) k_cma_finish_batch<<<n, 32, 0, s>>>(kp, st, pose_out);
+    if (op == 0) k_cma_reset_batch<<<n, 128, 0, s>>>(sel, t.k, t.st, t.ninst, t.joint);
+    if (op == 1) k_cma_tell_batch<<<n, kTellThreads, 0, s>>>(sel, t.k, t.st, t.y, t.params, t.loss);
+    if (op == 2) k_cma_finish_batch<<<n, 32, 0, s>>>(sel, t.k, t.st, t.pose);
     return cudaGetLastError();
 }
 

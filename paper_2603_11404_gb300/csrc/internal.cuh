@@ -133,10 +133,19 @@ cudaError_t launch_cma_ask(const CmaConst *k, int lam, CmaState *st, double *y, 
 cudaError_t launch_cma_tell(const CmaConst *k, CmaState *st, const double *y, const float *params,
                             const float *loss, cudaStream_t s);
 cudaError_t launch_cma_finish_frame(const CmaConst *k, CmaState *st, float *pose_out, cudaStream_t s);
-// op 0 reset from the estimate, 1 update, 2 frame epilogue; one block per instance
-cudaError_t launch_cma_batch(int op, int n, const CmaConst *const *kp, CmaState *const *st, const int *n_inst,
-                             const double *const *y, const float *const *params, const float *const *loss,
-                             float *const *pose_out, cudaStream_t s);
+// Device tables (one entry per instance) for the batched CMA-ES kernels.
+struct BatchTables {
+    const CmaConst **k = nullptr;
+    CmaState **st = nullptr;
+    const double **y = nullptr;
+    const float **params = nullptr, **loss = nullptr;
+    const float **joint = nullptr;   // joint readings for the reset, entries may be NULL; NULL table = none
+    float **pose = nullptr;          // frame estimates written by the epilogue
+    int *ninst = nullptr;
+};
+// op 0 reset from the estimate, 1 update, 2 frame epilogue; one block per
+// selected instance (sel[n] device indices, or NULL for instances 0..n-1)
+cudaError_t launch_cma_batch(int op, int n, const int *sel, const BatchTables &t, cudaStream_t s);
 
 }  // namespace trk
 
