@@ -5,7 +5,8 @@ executes anything in this package; only ``tests/``, ``__graft_entry__.smoke()``
 and the CPU-baseline leg of ``bench.py`` do.  It shares no code with the CUDA
 sources: the renderer is plain C in ``oracle.c`` (FP64 geometry, exact int64
 edge functions), the CMA-ES, random numbers and tracker are plain numpy in
-``cmaes.py``, ``philox.py`` and ``tracker.py``.
+``cmaes.py``, ``philox.py`` and ``tracker.py``, and the soft (differentiable)
+silhouette loss with its gradient is plain numpy in ``soft.py``.
 
 Scenes are duck-typed: any object with ``frames`` (parent, offset, axis, joint,
 coef), ``meshes`` (frame, verts, tris), ``q_lb``, ``q_ub``, ``K`` (fx, fy, cx,
