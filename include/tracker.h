@@ -287,6 +287,38 @@ trk_status track_frame_host(trk_cmaes *es, const uint8_t *mask_host, int32_t gen
                             void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Soft (differentiable) silhouette.  The paper fits with a differentiable
+ * renderer (Sec. III-A.2) and the MSE term of Eq. (render_loss); this is the
+ * soft form of that term, with a hand-written gradient:
+ *   d_t(p) = signed distance (px) from pixel centre p to projected triangle t
+ *            (+ inside, - outside; unsnapped projection),
+ *   a_t(p) = sigmoid(d_t(p) / sigma), 0 where d_t(p) < -14 sigma,
+ *   S(p)   = 1 - prod_t (1 - a_t(p)) over every triangle of every link,
+ *   L      = sum_p (S(p) - M(p))^2.
+ * Triangles with a flagged vertex or zero area are left out.  FP32
+ * throughout; sums use atomics, so the last bits may differ between runs.
+ * ------------------------------------------------------------------------- */
+
+/* loss_dev[lam] = L of each candidate of params_dev [lam*d]; with grad_dev
+ * [lam*d] not NULL also dL/dparams (physical units: rad, mm, rad of q-hat).
+ * The backward recomputes the forward tile by tile: no per-pixel state is
+ * kept between the passes.  sigma in [0.05, 64] px.  Asynchronous. */
+trk_status soft_eval(trk_tracker *t, const float *params_dev, int32_t lam, const uint32_t *mask_packed_dev,
+                     float sigma, float *loss_dev, float *grad_dev, void *stream);
+
+/* Gradient refinement after a tracked frame (call after track_frame_device
+ * on the same stream): the top_k candidates of the optimiser's last
+ * generation (lowest loss, then lowest index; top_k <= 32) take `steps` Adam
+ * steps (beta 0.9 / 0.999, eps 1e-8, step size lr in the optimiser's
+ * normalised units) on the soft loss; the refined candidate with the lowest
+ * fitness loss (the tracker's loss_kind, binary silhouette) replaces the
+ * frame's estimate if it beats the frame's best.  The estimate is written to
+ * pose_out_dev [d] (may be NULL); *picked_host (may be NULL; then the call is
+ * asynchronous) receives the index of the adopted refined candidate, or -1. */
+trk_status soft_refine(trk_cmaes *es, const uint32_t *mask_packed_dev, int32_t top_k, int32_t steps, float lr,
+                       float sigma, float *pose_out_dev, int32_t *picked_host, void *stream);
+
+/* ---------------------------------------------------------------------------
  * Heterogeneous batches: many instances (one- or two-instrument scenes with
  * their own meshes, image sizes and population sizes) in one persistent launch
  * per generation.  Not a paper feature: the paper tracks one scene per call;

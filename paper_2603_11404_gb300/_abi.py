@@ -91,6 +91,8 @@ SIGNATURES = {
     "batch_eval": [P, P, P, P, P, P],
     "batch_track_frame": [P, P, I32, P, I32, P],
     "batch_autotune": [P, P, P, I32, P, P, P, P],
+    "soft_eval": [P, P, I32, P, C.c_float, P, P, P],
+    "soft_refine": [P, P, I32, I32, C.c_float, C.c_float, P, P, P],
     "server_create": [I32, I32, I32, C.c_int64, I32, C.c_int64, I32, I32, P],
     "server_destroy": [P],
     "server_add_stream": [P, P, I32, I32, P],

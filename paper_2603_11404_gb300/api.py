@@ -140,6 +140,17 @@ class Tracker:
              _ptr(snap), _ptr(uv), _stream(stream))
         return loss, counts, snap, uv
 
+    def soft_eval(self, params: torch.Tensor, mask_packed: torch.Tensor, sigma: float = 1.0, grad: bool = False,
+                  stream=None):
+        """soft_eval: soft-silhouette loss [lam] (and dL/dparams [lam, d] when grad)."""
+        _check_dev(params, torch.float32, "params")
+        lam = params.shape[0]
+        loss = torch.empty(lam, dtype=torch.float32, device=params.device)
+        g = torch.empty((lam, self.d), dtype=torch.float32, device=params.device) if grad else None
+        call("soft_eval", self.h, _ptr(params), lam, _ptr(mask_packed), float(sigma), _ptr(loss), _ptr(g),
+             _stream(stream))
+        return (loss, g) if grad else loss
+
     def render(self, state: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         """tracker_render: one state [d] -> packed silhouette int32 [H, ceil(W/32)]."""
         _check_dev(state, torch.float32, "state")
@@ -246,6 +257,18 @@ class CMAES:
         call("track_frame_host", self.h, _ptr(mask_u8), int(generations), _ptr(jr), _ptr(pose), C.byref(bl),
              _stream(stream))
         return pose, bl.value
+
+    def refine(self, mask_packed: torch.Tensor, top_k: int = 8, steps: int = 10, lr: float = 0.05,
+               sigma: float = 1.0, pose_out: torch.Tensor | None = None, stream=None):
+        """soft_refine: Adam steps on the soft loss for the last generation's top_k
+        candidates; returns (estimate [d] on the device, index of the adopted
+        refined candidate or -1)."""
+        if pose_out is None:
+            pose_out = torch.empty(self.d, dtype=torch.float32, device="cuda")
+        picked = C.c_int32()
+        call("soft_refine", self.h, _ptr(mask_packed), int(top_k), int(steps), float(lr), float(sigma),
+             _ptr(pose_out), C.byref(picked), _stream(stream))
+        return pose_out, picked.value
 
     def save(self, stream=None) -> bytes:
         n = C.c_size_t()
@@ -415,3 +438,26 @@ class Server:
             if a == 0 and q == 0:
                 break
         return out + self.poll(wait=True)
+
+
+class SoftSilhouetteLoss(torch.autograd.Function):
+    """Soft-silhouette loss per candidate as a differentiable torch op:
+    forward = soft_eval without gradient; backward = soft_eval with gradient
+    (it recomputes the forward tile by tile), scaled by the incoming grad."""
+
+    @staticmethod
+    def forward(ctx, params, tracker, mask_packed, sigma=1.0):
+        p = params.detach().contiguous()
+        ctx.tracker, ctx.mask, ctx.sigma = tracker, mask_packed, sigma
+        ctx.save_for_backward(p)
+        return tracker.soft_eval(p, mask_packed, sigma)
+
+    @staticmethod
+    def backward(ctx, grad_loss):
+        (p,) = ctx.saved_tensors
+        _, g = ctx.tracker.soft_eval(p, ctx.mask, ctx.sigma, grad=True)
+        return grad_loss.to(g.dtype)[:, None] * g, None, None, None
+
+
+def soft_silhouette_loss(params: torch.Tensor, tracker: Tracker, mask_packed: torch.Tensor, sigma: float = 1.0):
+    return SoftSilhouetteLoss.apply(params, tracker, mask_packed, sigma)

@@ -68,6 +68,7 @@ static void tracker_free(trk_tracker *t)
     cudaFree(t->tris);
     cudaFree(t->snap);
     cudaFree(t->zero_mask);
+    soft_free(t);
     delete t;
 }
 
@@ -326,6 +327,7 @@ static void cmaes_free(trk_cmaes *es)
     cudaFree(es->joint);
     cudaFree(es->pose);
     cudaFree(es->done);
+    refine_free(es);
     delete es;
 }
 

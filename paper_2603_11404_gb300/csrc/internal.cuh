@@ -161,6 +161,7 @@ struct trk_tracker {
     int2 *snap = nullptr;       // scratch [lambda_max * n_inst * V]
     uint32_t *zero_mask = nullptr;
     trk::LaunchCfg lc{};
+    void *soft = nullptr;       // soft-silhouette scratch, allocated on first use
 };
 
 struct trk_cmaes {
@@ -178,7 +179,13 @@ struct trk_cmaes {
     float *joint = nullptr;     // [3*n_inst]
     float *pose = nullptr;      // [d]
     unsigned *done = nullptr;   // CTA ticket counter of the fused generation kernel
+    void *refine = nullptr;     // gradient-refinement buffers, allocated on first use
     int lam = 0, d = 0;
 };
+
+namespace trk {
+void soft_free(trk_tracker *t);      // releases trk_tracker::soft
+void refine_free(trk_cmaes *es);     // releases trk_cmaes::refine
+}  // namespace trk
 
 

@@ -1,0 +1,122 @@
+"""Soft silhouette on the GPU (soft_eval, the autograd op, soft_refine) against
+the FP64 oracle: losses, analytic gradients and FP64 central differences."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import soft
+from paper_2603_11404_gb300 import workload as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_11404_gb300 import build
+    build.build()
+    from paper_2603_11404_gb300 import api as a
+    return a
+
+
+def _case(api, mesh, cam, n_inst, K, seed, lam):
+    sc = wl.make_scene(mesh, cam, n_instruments=n_inst, K=K)
+    rng = np.random.default_rng(seed)
+    gt = np.concatenate([wl.sample_state(rng, sc.K) for _ in range(n_inst)])
+    M = wl.corrupt_mask(oracle.render(sc, gt), rng)
+    P = wl.population_around(rng, gt, lam)
+    tr = api.Tracker(sc, lambda_max=max(lam, 1))
+    Mp = tr.pack_mask(torch.from_numpy(M).cuda())
+    return sc, tr, M, Mp, P
+
+
+def _rel(g, ref, s):
+    return np.linalg.norm((g - ref) * s) / np.linalg.norm(ref * s)
+
+
+@pytest.mark.parametrize("which", ["c1", "bimanual", "lookat"])
+def test_soft_loss_and_gradient_match_oracle(api, which):
+    if which == "c1":
+        sc, tr, M, Mp, P = _case(api, "c1", "c1", 1, None, 11, 4)
+    elif which == "bimanual":
+        sc, tr, M, Mp, P = _case(api, "800", "c1", 2, wl.Intrinsics(150.0, 150.0, 50.0, 38.5, 101, 77), 12, 3)
+    else:
+        sc = wl.make_scene("c1", "c1", rot_param=wl.ROT_LOOKAT)
+        rng = np.random.default_rng(13)
+        gt = wl.sample_state(rng, sc.K)
+        gt[:3] = [0.2, -0.4, 0.3]  # look-at angles (alpha, beta, gamma)
+        M = wl.corrupt_mask(oracle.render(sc, gt), rng)
+        P = wl.population_around(rng, gt, 3)
+        tr = api.Tracker(sc, lambda_max=3)
+        Mp = tr.pack_mask(torch.from_numpy(M).cuda())
+    loss, g = tr.soft_eval(torch.from_numpy(P).cuda(), Mp, grad=True)
+    loss, g = loss.cpu().numpy(), g.cpu().numpy()
+    s = wl.default_scales(sc.d)
+    for c in range(P.shape[0]):
+        L, gref = soft.soft_grad(sc, P[c].astype(np.float64), M)
+        assert loss[c] == pytest.approx(L, rel=1e-4), c
+        assert _rel(g[c], gref, s) < 1e-3, (c, g[c], gref)
+
+
+def test_soft_gradient_matches_fp64_central_differences(api):
+    sc, tr, M, Mp, P = _case(api, "c1", "c1", 1, None, 21, 2)
+    _, g = tr.soft_eval(torch.from_numpy(P).cuda(), Mp, grad=True)
+    g = g.cpu().numpy()
+    s = wl.default_scales(9)
+    for c in range(P.shape[0]):
+        x = P[c].astype(np.float64)
+        fd = np.array([(soft.soft_loss(sc, x + e, M) - soft.soft_loss(sc, x - e, M)) / (2 * e[k])
+                       for k, e in enumerate(np.eye(9) * 1e-4 * s)])
+        assert _rel(g[c], fd, s) < 1e-3, (c, g[c], fd)
+
+
+def test_soft_full_size_candidate_matches_oracle(api):
+    """640x512, 20k-triangle mesh: one candidate's loss and gradient."""
+    sc, tr, M, Mp, P = _case(api, "c2", "c2", 1, None, 31, 64)
+    loss, g = tr.soft_eval(torch.from_numpy(P).cuda(), Mp, grad=True)
+    L, gref = soft.soft_grad(sc, P[5].astype(np.float64), M)
+    assert loss[5].item() == pytest.approx(L, rel=1e-4)
+    assert _rel(g[5].cpu().numpy(), gref, wl.default_scales(9)) < 1e-3
+    # the rest of the population: the loss alone
+    for c in (0, 63):
+        assert loss[c].item() == pytest.approx(soft.soft_loss(sc, P[c].astype(np.float64), M), rel=1e-4)
+
+
+def test_autograd_function_backward_is_the_hand_written_gradient(api):
+    sc, tr, M, Mp, P = _case(api, "c1", "c1", 1, None, 41, 5)
+    x = torch.from_numpy(P).cuda().requires_grad_(True)
+    w = torch.arange(1, 6, dtype=torch.float32, device="cuda")
+    L = api.soft_silhouette_loss(x, tr, Mp)
+    (L * w).sum().backward()
+    _, g = tr.soft_eval(torch.from_numpy(P).cuda(), Mp, grad=True)
+    assert torch.allclose(x.grad, w[:, None] * g, rtol=1e-4, atol=1e-3)
+    assert torch.allclose(L, tr.soft_eval(torch.from_numpy(P).cuda(), Mp), rtol=1e-6)
+
+
+def test_refine_improves_or_keeps_the_estimate(api):
+    sc, tr, M, Mp, P = _case(api, "c1", "c1", 1, None, 51, 16)
+    tr2 = api.Tracker(sc, loss_kind=wl.LOSS_XOR, lambda_max=16)
+    init = P[0].astype(np.float64)
+    es = api.CMAES(tr2, 16, init, wl.default_scales(9), sigma0=1.0, seed=7)
+    es.track_frame(Mp, 5)
+    before = es.state()["best_loss"]
+    pose, picked = es.refine(Mp, top_k=8, steps=10, lr=0.05)
+    st = es.state()
+    assert st["best_loss"] <= before
+    assert picked in range(-1, 8)
+    assert (picked >= 0) == (st["best_loss"] < before)
+    # the estimate is the adopted candidate and its fitness is the reported best
+    l = tr2.eval_population(pose[None].contiguous(), Mp)
+    assert l.item() == st["best_loss"]
+    assert np.array_equal(pose.cpu().numpy(), st["best_x"])
+
+
+def test_soft_rejects_bad_arguments(api):
+    from paper_2603_11404_gb300._abi import TrkError
+    sc, tr, M, Mp, P = _case(api, "c1", "c1", 1, None, 61, 2)
+    with pytest.raises(TrkError):
+        tr.soft_eval(torch.from_numpy(P).cuda(), Mp, sigma=0.0)
+    empty = torch.zeros((0, 9), dtype=torch.float32, device="cuda")
+    assert tr.soft_eval(empty, Mp).numel() == 0
