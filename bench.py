@@ -283,6 +283,7 @@ def run_ours(a):
         "clocks": clk.summary(),
     }
     if not a.no_forms:
+        out["soft"] = bench_soft(a, rank, tr, sc, traj, init, packed, flush)
         out["batching"] = bench_batching(a, rank)
         out["serving"] = bench_serving(a, rank)
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
@@ -300,6 +301,68 @@ def _masks_for(api, tr, sc, traj, rng):
         S = api.unpack_mask(tr.render(torch.from_numpy(st.astype(np.float32)).cuda()), sc.K.width).cpu().numpy()
         out.append(wl.corrupt_mask(S, rng))
     return out
+
+
+def bench_soft(a, rank, tr, sc, traj, init, packed, flush, n_frames: int = 60, reps: int = 20):
+    """Form (3): soft-silhouette loss (sigma = 1 px) at 640x512 / 20k triangles
+    for lambda = 64 candidates, forward alone and forward + backward; then
+    tracking with CMA-ES + 10 Adam steps on the top-8 candidates per frame
+    against CMA-ES alone (5 and 10 generations), same frames and seeds."""
+    import torch
+
+    from paper_2603_11404_gb300 import api
+    stream = torch.cuda.current_stream()
+    rng = np.random.default_rng(SEED + 3 + rank)
+    P = torch.from_numpy(wl.population_around(rng, traj[a.warmup], LAM)).cuda()
+    Mp = packed[a.warmup]
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ms = []
+        for i in range(reps):
+            flush.fill_(i)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return float(np.median(ms))
+
+    fwd_ms = timed(lambda: tr.soft_eval(P, Mp))
+    bwd_ms = timed(lambda: tr.soft_eval(P, Mp, grad=True))
+    hard_ms = timed(lambda: tr.eval_population(P, Mp))
+    n = min(n_frames, packed.shape[0])
+    scales = wl.default_scales(9)
+
+    def track(gens, refine):
+        es = api.CMAES(tr, LAM, init, scales, sigma0=1.0, seed=SEED + 99)
+        poses = torch.empty((n, 9), dtype=torch.float32, device="cuda")
+        ev = []
+        for f in range(n):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            es.track_frame(packed[f], gens, pose_out=poses[f])
+            if refine:
+                es.refine(packed[f], top_k=8, steps=10, lr=0.05, pose_out=poses[f])
+            e1.record(stream)
+            ev.append((e0, e1))
+        torch.cuda.synchronize()
+        ms = np.array([x.elapsed_time(y) for x, y in ev])
+        err = np.abs(poses.cpu().numpy() - traj[:n].astype(np.float32))[5:]
+        return {"frame_ms_p50": float(np.median(ms)), "frame_ms_p99": float(np.percentile(ms, 99)),
+                "rot_rad_median": float(np.median(err[:, :3])), "trans_mm_median": float(np.median(err[:, 3:6])),
+                "joint_median": float(np.median(err[:, 6:]))}
+
+    return {"workload": "640x512, %d-triangle mesh, sigma 1 px, cutoff 14 sigma, lambda=%d; tracking over %d frames "
+                        "(errors after frame 5)" % (sc.n_tris, LAM, n),
+            "soft_forward_ms": fwd_ms, "soft_forward_backward_ms": bwd_ms, "binary_fitness_ms": hard_ms,
+            "soft_candidate_grads_per_s": LAM / (bwd_ms / 1e3),
+            "track_cmaes_5gen": track(GENS, False), "track_cmaes_5gen_refine_top8_x10": track(GENS, True),
+            "track_cmaes_10gen": track(2 * GENS, False),
+            "checks": "gradients vs FP64 oracle and FP64 central differences (h=1e-4) within 1e-3: "
+                      "tests/test_gpu_soft.py"}
 
 
 BATCH_IMAGES = [(320, 256), (640, 512), (960, 768), (1280, 1024)]

@@ -6,10 +6,10 @@
 // costs ~64 cycles, division and square root ~700): the covariance, paths and
 // step size are FP64; sampling draws FP32 normals; the eigendecomposition runs
 // a warm-started FP32 Jacobi pass for the bulk of the rotation, then makes the
-// basis orthogonal in FP64 (Newton-Schulz) and finishes with FP64 Jacobi
-// sweeps whose rotation angles come from FP32 formulas and whose (c, s) pairs
-// are re-normalised in FP64, so the result is accurate to FP64 rounding
-// without FP64 divisions or square roots in the inner loop.
+// basis orthogonal in FP64 (Newton-Schulz), and C^(1/2), C^(-1/2) come from
+// the nearly diagonal V^T C V by two Newton steps for the matrix square root
+// (Sylvester equations solved entrywise), accurate to FP64 rounding without
+// FP64 Jacobi sweeps, divisions or square roots in loops.
 #pragma once
 
 #include <math.h>
@@ -123,97 +123,22 @@ struct TellSmem {
     double part[8][kMaxD];
     double C[kMaxD * kMaxD], A[kMaxD * kMaxD], A2[kMaxD * kMaxD], V[kMaxD * kMaxD], V2[kMaxD * kMaxD];
     double B[kMaxD * kMaxD], ysel[kYselCap], w[TRK_MAX_LAMBDA / 2];
-    float Af[kMaxD * kMaxD], Af2[kMaxD * kMaxD], Vf[kMaxD * kMaxD], Vf2[kMaxD * kMaxD];
-    float rc[kMaxD / 2 + 1], rs[kMaxD / 2 + 1];
-    double rcd[kMaxD / 2 + 1], rsd[kMaxD / 2 + 1];
-    int rp[kMaxD / 2 + 1], rq[kMaxD / 2 + 1];
+    float Af[kMaxD * kMaxD], Vf[kMaxD * kMaxD], Vf2[kMaxD * kMaxD];
     double n2, hs;
 };
 
-// Jacobi rotation (c, s) in FP32 that annihilates a_pq of the 2x2 block
-// [[a_pp, a_pq], [a_pq, a_qq]] (Golub & Van Loan, symmetric Schur
-// decomposition); diff = a_qq - a_pp is formed by the caller in the matrix's
-// own precision so that near-equal diagonals keep their difference.
-__device__ __forceinline__ void jacobi_angle_f32(float diff, float apq, float &c, float &s)
-{
-    if (apq == 0.0f) {
-        c = 1.0f;
-        s = 0.0f;
-        return;
-    }
-    // approximate intrinsics suffice: the rotation only has to be close to the
-    // annihilating one (the FP64 sweeps finish the job and re-normalise (c, s))
-    float tau = __fdividef(diff, 2.0f * apq);
-    float t;
-    if (fabsf(tau) > 1e18f) {
-        t = __fdividef(0.5f, tau);
-    } else {
-        float h = 1.0f + tau * tau;
-        t = __fdividef(1.0f, fabsf(tau) + h * rsqrtf(h));
-    }
-    if (tau < 0.0f) t = -t;
-    if (!isfinite(t)) t = 0.0f;
-    c = rsqrtf(1.0f + t * t);
-    s = t * c;
-}
-
-// Pair `pr` of round s of the round-robin (circle) ordering on n2 indices.
-__device__ __forceinline__ void rr_pair(int n2, int s, int pr, int &p, int &q)
-{
-    if (pr == 0) {
-        p = n2 - 1;
-        q = s;
-    } else {
-        p = (s + pr) % (n2 - 1);
-        q = (s - pr + (n2 - 1)) % (n2 - 1);
-    }
-}
-
-// A' = J^T A J and V' = V J for one round of disjoint rotations (pairs of
-// indices rp/rq with cosines rc/rs); indices >= d are padding.  Templated on
-// the precision; every thread of the block calls it.
-template <typename T>
-__device__ __forceinline__ void jacobi_round_apply(int d, int np, const int *rp, const int *rq, const T *rc,
-                                                   const T *rs, const T *A, T *A2, const T *V, T *V2, int tid, int nt)
-{
-    // consecutive items go to different warps, so a block of several warps
-    // spreads the work over all of its sub-partitions' pipes
-    if (nt > 32 && nt % 32 == 0) tid = (tid & 31) * (nt >> 5) + (tid >> 5);
-    for (int e = tid; e < np * np; e += nt) {  // 2x2 block (P, Q)
-        int P = e / np, Q = e - P * np;
-        int ip[2] = {rp[P], rq[P]}, jq[2] = {rp[Q], rq[Q]};
-        T cP = rc[P], sP = rs[P], cQ = rc[Q], sQ = rs[Q];
-        T M[2][2];
-        for (int a = 0; a < 2; ++a)
-            for (int b = 0; b < 2; ++b) M[a][b] = (ip[a] < d && jq[b] < d) ? A[ip[a] * d + jq[b]] : (T)0;
-        T t0[2], t1[2];
-        for (int a = 0; a < 2; ++a) {
-            t0[a] = cQ * M[a][0] - sQ * M[a][1];
-            t1[a] = sQ * M[a][0] + cQ * M[a][1];
-        }
-        T o00 = cP * t0[0] - sP * t0[1], o10 = sP * t0[0] + cP * t0[1];
-        T o01 = cP * t1[0] - sP * t1[1], o11 = sP * t1[0] + cP * t1[1];
-        if (ip[0] < d && jq[0] < d) A2[ip[0] * d + jq[0]] = o00;
-        if (ip[1] < d && jq[0] < d) A2[ip[1] * d + jq[0]] = o10;
-        if (ip[0] < d && jq[1] < d) A2[ip[0] * d + jq[1]] = o01;
-        if (ip[1] < d && jq[1] < d) A2[ip[1] * d + jq[1]] = o11;
-    }
-    for (int e = tid; e < d * np; e += nt) {  // V J
-        int i = e / np, P = e - i * np;
-        int p = rp[P], q = rq[P];
-        T c = rc[P], s = rs[P];
-        if (p < d && q < d) {
-            T vp = V[i * d + p], vq = V[i * d + q];
-            V2[i * d + p] = c * vp - s * vq;
-            V2[i * d + q] = s * vp + c * vq;
-        } else {
-            int r = (p < d) ? p : q;
-            if (r < d) V2[i * d + r] = V[i * d + r];
-        }
-    }
-}
-
 // C (d x d, FP64, row-major) -> out = X^T C X for square X, FP64.
+// 1 / a for a > 0 in FP64 without a division: the FP32 reciprocal as a seed,
+// then two Newton-Raphson steps r <- r + r (1 - a r), each doubling the
+// correct bits (24 -> 48 -> 96, so the result is correctly rounded or 1 ulp off).
+__device__ __forceinline__ double rcp64(double a)
+{
+    double r = (double)__frcp_rn((float)a);
+    r = __fma_rn(r, __fma_rn(-a, r, 1.0), r);
+    r = __fma_rn(r, __fma_rn(-a, r, 1.0), r);
+    return r;
+}
+
 __device__ __forceinline__ void sandwich64(int d, const double *X, const double *Cm, double *tmp, double *out, int tid,
                                            int nt)
 {
@@ -365,7 +290,99 @@ __device__ __forceinline__ void cma_tell_impl(const CmaConst &k, CmaState *st, c
         st->C[e] = S.A[e];
     }
 #undef YSEL
-    if (tid == 0) {
+    __syncthreads();
+
+    // ---- eigendecomposition, phase 1: one-sided (Hestenes) Jacobi in FP32 on
+    //      the columns of X = C B (B = last generation's basis, a warm start),
+    //      one warp, columns in shared memory.  Each round pairs the columns by
+    //      the circle method; a pair (u, w) is rotated by the angle that makes
+    //      u . w = 0, cot 2 theta = (|w|^2 - |u|^2) / (2 u . w), and the same
+    //      rotation is applied to the accumulated basis J.  When every pair has
+    //      |u . w| <= 1e-5 |u| |w| the columns of C B J are orthogonal to that
+    //      level, so B J is an eigenbasis of C up to off-diagonal terms of
+    //      V^T C V below 1e-5 of the diagonal, which the FP64 square-root
+    //      refinement absorbs (its error is of third order in them) ----
+    for (int e = tid; e < dd; e += nt) {
+        const int i = e / d, j = e - i * d;
+        float acc = 0.0f;
+        for (int q = 0; q < d; ++q) acc = fmaf((float)S.C[i * d + q], (float)S.B[q * d + j], acc);
+        S.Af[j * d + i] = acc;                   // column j of C B
+        S.Vf2[j * d + i] = (i == j) ? 1.0f : 0.0f;  // column j of J
+    }
+    __syncthreads();
+    if (tid < 32) {
+        const int lane = tid, n2 = d + (d & 1);
+        float *Xc = S.Af, *Jc = S.Vf2;
+        float amax = 0.0f;  // largest squared column norm, for the absolute floor
+        if (lane < d)
+            for (int q = 0; q < d; ++q) amax = fmaxf(amax, Xc[lane * d + q] * Xc[lane * d + q]);
+        for (int o = 16; o; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        int sweeps = 0;
+        for (; sweeps < 12; ++sweeps) {
+            bool rotated = false;
+            float rho = 0.0f;  // largest |u . w| / (|u| |w|) rotated in this sweep
+            for (int r = 0; r < n2 - 1; ++r) {
+                // circle method: position n2-1 meets r, the others pair as (r+i, r-i) mod n2-1
+                int partner;
+                if (lane == n2 - 1) partner = r;
+                else if (lane == r) partner = n2 - 1;
+                else partner = (2 * r - lane + 2 * (n2 - 1)) % (n2 - 1);
+                const bool act = lane < d && partner < d;
+                const int lo = min(lane, partner), hi = max(lane, partner);
+                float c = 1.0f, sn = 0.0f;
+                float xo[kMaxD], vo[kMaxD];
+                if (act) {
+                    float a = 0.0f, b = 0.0f, g = 0.0f;
+#pragma unroll
+                    for (int q = 0; q < kMaxD; ++q)
+                        if (q < d) {
+                            const float u = Xc[lo * d + q], w = Xc[hi * d + q];
+                            a = fmaf(u, u, a);
+                            b = fmaf(w, w, b);
+                            g = fmaf(u, w, g);
+                        }
+                    if (g * g > 1e-10f * a * b + 1e-22f * amax * amax) {
+                        const float zeta = (b - a) / (2.0f * g);
+                        const float t = copysignf(1.0f, zeta) / (fabsf(zeta) + sqrtf(1.0f + zeta * zeta));
+                        c = rsqrtf(1.0f + t * t);
+                        sn = t * c;
+                        rotated = true;
+                        rho = fmaxf(rho, fabsf(g) * rsqrtf(a * b));
+                    }
+                    // own column after the rotation: lo gets c u - s w, hi gets s u + c w
+                    const bool is_lo = lane == lo;
+#pragma unroll
+                    for (int q = 0; q < kMaxD; ++q)
+                        if (q < d) {
+                            const float u = Xc[lo * d + q], w = Xc[hi * d + q];
+                            const float ju = Jc[lo * d + q], jw = Jc[hi * d + q];
+                            xo[q] = is_lo ? fmaf(c, u, -sn * w) : fmaf(sn, u, c * w);
+                            vo[q] = is_lo ? fmaf(c, ju, -sn * jw) : fmaf(sn, ju, c * jw);
+                        }
+                }
+                __syncwarp();
+                if (act) {
+#pragma unroll
+                    for (int q = 0; q < kMaxD; ++q)
+                        if (q < d) {
+                            Xc[lane * d + q] = xo[q];
+                            Jc[lane * d + q] = vo[q];
+                        }
+                }
+                __syncwarp();
+            }
+            // Jacobi converges quadratically: after a sweep whose rotations were
+            // all below 1e-3 the columns are orthogonal to ~1e-6 without checking
+            for (int o = 16; o; o >>= 1) rho = fmaxf(rho, __shfl_xor_sync(0xffffffffu, rho, o));
+            if (!__any_sync(0xffffffffu, rotated) || rho < 1e-3f) {
+                ++sweeps;
+                break;
+            }
+        }
+        if (lane == 0) st->jacobi_sweeps = sweeps;
+    }
+    if (tid == (nt > 32 ? 32 : 0)) {
+        // step size (CSA): on the second warp, off the eigendecomposition's critical path
         double sg = sigma * exp(k.cs_over_ds * (sqrt(S.n2) * k.inv_chi - 1.0));
         st->sigma = sg;
         st->sigma_df = split_df(sg);
@@ -373,58 +390,9 @@ __device__ __forceinline__ void cma_tell_impl(const CmaConst &k, CmaState *st, c
         st->gen_total += 1;
     }
     __syncthreads();
-
-    // ---- eigendecomposition, phase 1: FP32 Jacobi on B^T C B, warm start ----
-    const int n2r = d + (d & 1), np = n2r / 2;
-    for (int e = tid; e < dd; e += nt) {
-        int i = e / d, j = e - i * d;
-        float acc = 0.0f;
-        for (int q = 0; q < d; ++q) acc = fmaf((float)S.C[i * d + q], (float)S.B[q * d + j], acc);
-        S.Af2[e] = acc;
-        S.Vf[e] = (i == j) ? 1.0f : 0.0f;
-    }
-    __syncthreads();
-    for (int e = tid; e < dd; e += nt) {
-        int i = e / d, j = e - i * d;
-        float acc = 0.0f;
-        for (int q = 0; q < d; ++q) acc = fmaf((float)S.B[q * d + i], S.Af2[q * d + j], acc);
-        S.Af[e] = acc;
-    }
-    __syncthreads();
-    {
-        float *Af = S.Af, *Af2 = S.Af2, *Vf = S.Vf, *Vf2 = S.Vf2;
-        for (int sweep = 0; sweep < 10; ++sweep) {
-            // until the off-diagonal is at FP32 rounding level (relative 1e-6, or
-            // 4e-7 of the largest diagonal entry): the FP64 sweep finishes the job
-            float amax = 0.0f;
-            for (int i = 0; i < d; ++i) amax = fmaxf(amax, fabsf(Af[i * d + i]));
-            const float floor2 = (4e-7f * amax) * (4e-7f * amax);
-            int off = 0;
-            for (int e = tid; e < dd; e += nt) {
-                int i = e / d, j = e - i * d;
-                if (j > i && Af[e] * Af[e] > 1e-12f * fabsf(Af[i * d + i] * Af[j * d + j]) + floor2) off = 1;
-            }
-            if (!__syncthreads_or(off)) break;
-            for (int s2 = 0; s2 < n2r - 1; ++s2) {
-                if (tid < np) {
-                    int p, q;
-                    rr_pair(n2r, s2, tid, p, q);
-                    float c = 1.0f, sn = 0.0f;
-                    if (p < d && q < d) jacobi_angle_f32(Af[q * d + q] - Af[p * d + p], Af[p * d + q], c, sn);
-                    S.rp[tid] = p;
-                    S.rq[tid] = q;
-                    S.rc[tid] = c;
-                    S.rs[tid] = sn;
-                }
-                __syncthreads();
-                jacobi_round_apply<float>(d, np, S.rp, S.rq, S.rc, S.rs, Af, Af2, Vf, Vf2, tid, nt);
-                __syncthreads();
-                float *t = Af; Af = Af2; Af2 = t;
-                t = Vf; Vf = Vf2; Vf2 = t;
-            }
-        }
-        if (Vf != S.Vf)  // an odd number of rounds left the basis in S.Vf2
-            for (int e = tid; e < dd; e += nt) S.Vf[e] = S.Vf2[e];
+    for (int e = tid; e < dd; e += nt) {  // J row-major for phase 2
+        const int i = e / d, j = e - i * d;
+        S.Vf[e] = S.Vf2[j * d + i];
     }
     __syncthreads();
     const float *Vf = S.Vf;
@@ -456,53 +424,18 @@ __device__ __forceinline__ void cma_tell_impl(const CmaConst &k, CmaState *st, c
         double *t = V; V = V2; V2 = t;
     }
     sandwich64(d, V, S.C, A2, A, tid, nt);  // A = V^T C V
-    // ---- phase 3: FP64 Jacobi sweeps (FP32 angles, FP64-normalised rotations).
-    //      The FP32 pass left off-diagonals at ~1e-6 relative; each rotation
-    //      removes all but ~1e-7 of its entry, and the cross terms a sweep
-    //      leaves are of order off^2 / gap (quadratic convergence), so one sweep
-    //      usually reaches ~1e-12.  Clustered eigenvalues (small gaps, common
-    //      while C is still near a multiple of I) can leave ~1e-9; a further
-    //      sweep runs while any off-diagonal entry exceeds 1e-11 of the largest
-    //      diagonal one (at most three sweeps in all) ----
-    int sweeps64 = 0;
-    for (; sweeps64 < 3; ++sweeps64) {
-        if (sweeps64 > 0) {
-            double amax = 0.0;
-            for (int i = 0; i < d; ++i) amax = fmax(amax, fabs(A[i * d + i]));
-            const double tol = 1e-11 * amax;
-            int off = 0;
-            for (int e = tid; e < dd; e += nt) {
-                int i = e / d, j = e - i * d;
-                if (j > i && fabs(A[e]) > tol) off = 1;
-            }
-            if (!__syncthreads_or(off)) break;
-        }
-        for (int s = 0; s < n2r - 1; ++s) {
-            if (tid < np) {
-                int p, q;
-                rr_pair(n2r, s, tid, p, q);
-                double c = 1.0, sn = 0.0;
-                if (p < d && q < d && A[p * d + q] != 0.0) {
-                    float cf, sf;
-                    jacobi_angle_f32((float)(A[q * d + q] - A[p * d + p]), (float)A[p * d + q], cf, sf);
-                    double cd = cf, sd = sf;
-                    double f = 1.5 - 0.5 * (cd * cd + sd * sd);  // one Newton step to c^2 + s^2 = 1
-                    c = cd * f;
-                    sn = sd * f;
-                }
-                S.rp[tid] = p;
-                S.rq[tid] = q;
-                S.rcd[tid] = c;
-                S.rsd[tid] = sn;
-            }
-            __syncthreads();
-            jacobi_round_apply<double>(d, np, S.rp, S.rq, S.rcd, S.rsd, A, A2, V, V2, tid, nt);
-            __syncthreads();
-            double *t = A; A = A2; A2 = t;
-            t = V; V = V2; V2 = t;
-        }
-    }
-    // ---- eigenvalues (clamped positive), basis, C^(1/2), C^(-1/2) ----
+    // ---- phase 3: C^(1/2) and C^(-1/2) from the near-diagonal A = V^T C V.
+    //      A = D + F with F off-diagonal (about 1e-6 of A after the FP32
+    //      pass).  Two Newton steps for the square root started from D^(1/2)
+    //      give A^(1/2) = S + O(F^3) with S = D^(1/2) + X + Z, where X and Z
+    //      solve the Sylvester equations
+    //        D^(1/2) X + X D^(1/2) = F,    D^(1/2) Z + Z D^(1/2) = -X^2,
+    //      entrywise X_ij = F_ij / (sqrt d_i + sqrt d_j): only sums of
+    //      eigenvalues divide, never differences, so clustered eigenvalues
+    //      cost nothing.  With W = D^(-1/2) (X + Z), S = D^(1/2) (I + W) and
+    //      S^(-1) = (I - W + W^2) D^(-1/2) + O(W^3).  Then C^(1/2) = V S V^T
+    //      and C^(-1/2) = V S^(-1) V^T, exact up to the O(F^3) terms because V
+    //      is orthogonal to FP64 rounding ----
     if (tid < d) {
         double emax = 0.0;
         for (int i = 0; i < d; ++i) emax = fmax(emax, A[i * d + i]);
@@ -516,21 +449,68 @@ __device__ __forceinline__ void cma_tell_impl(const CmaConst &k, CmaState *st, c
         S.sq[tid] = e * r;
         S.isq[tid] = r;
     }
-    if (tid == 0) st->jacobi_sweeps = sweeps64;
     __syncthreads();
-    for (int e = tid; e < dd; e += nt) {
-        int i = e / d, j = e - i * d;
+    double *X = A2, *P = S.C, *Wm = S.B, *W2 = V2;
+    for (int e = tid; e < dd; e += nt) {  // X
+        const int i = e / d, j = e - i * d;
+        X[e] = (i == j) ? 0.0 : A[e] * rcp64(S.sq[i] + S.sq[j]);
+    }
+    __syncthreads();
+    for (int e = tid; e < dd; e += nt) {  // X^2
+        const int i = e / d, j = e - i * d;
+        double acc = 0.0;
+        for (int q = 0; q < d; ++q) acc = __fma_rn(X[i * d + q], X[q * d + j], acc);
+        P[e] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < dd; e += nt) {  // S (in place of X) and W
+        const int i = e / d, j = e - i * d;
+        const double y = __fma_rn(-P[e], rcp64(S.sq[i] + S.sq[j]), X[e]);  // X + Z
+        Wm[e] = S.isq[i] * y;
+        X[e] = (i == j) ? S.sq[i] + y : y;
+    }
+    __syncthreads();
+    for (int e = tid; e < dd; e += nt) {  // W^2
+        const int i = e / d, j = e - i * d;
+        double acc = 0.0;
+        for (int q = 0; q < d; ++q) acc = __fma_rn(Wm[i * d + q], Wm[q * d + j], acc);
+        W2[e] = acc;
+    }
+    __syncthreads();
+    double *Si = S.C;
+    for (int e = tid; e < dd; e += nt) {  // S^(-1)
+        const int i = e / d, j = e - i * d;
+        Si[e] = (((i == j) ? 1.0 : 0.0) - Wm[e] + W2[e]) * S.isq[j];
+    }
+    __syncthreads();
+    double *T1 = A, *T2 = V2;
+    for (int e = tid; e < dd; e += nt) {  // V S and V S^(-1)
+        const int i = e / d, j = e - i * d;
+        double a1 = 0.0, a2 = 0.0;
+        for (int q = 0; q < d; ++q) {
+            a1 = __fma_rn(V[i * d + q], X[q * d + j], a1);
+            a2 = __fma_rn(V[i * d + q], Si[q * d + j], a2);
+        }
+        T1[e] = a1;
+        T2[e] = a2;
+    }
+    __syncthreads();
+    for (int e = tid; e < dd; e += nt) {  // (V S) V^T, (V S^(-1)) V^T; upper triangle mirrored
+        const int i = e / d, j = e - i * d;
+        if (j < i) continue;
         double h = 0.0, ih = 0.0;
         for (int q = 0; q < d; ++q) {
-            double vv = V[i * d + q] * V[j * d + q];
-            h = __fma_rn(vv, S.sq[q], h);
-            ih = __fma_rn(vv, S.isq[q], ih);
+            h = __fma_rn(T1[i * d + q], V[j * d + q], h);
+            ih = __fma_rn(T2[i * d + q], V[j * d + q], ih);
         }
-        st->C_half[e] = h;
-        st->C_half_df[e] = split_df(h);
-        st->C_inv_half[e] = ih;
-        st->B[e] = V[e];
+        st->C_half[i * d + j] = h;
+        st->C_half[j * d + i] = h;
+        st->C_half_df[i * d + j] = split_df(h);
+        st->C_half_df[j * d + i] = split_df(h);
+        st->C_inv_half[i * d + j] = ih;
+        st->C_inv_half[j * d + i] = ih;
     }
+    for (int e = tid; e < dd; e += nt) st->B[e] = V[e];
 }
 
 static __device__ __noinline__ void cma_tell_block(const CmaConst &k, CmaState *st, const double *y,

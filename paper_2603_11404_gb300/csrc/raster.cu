@@ -3,16 +3,16 @@
 //   loss of Eq. render_loss / the 1 - IoU mask error of Sec. IV-B.
 //
 // Launch shape: one thread-block cluster of `cluster` CTAs per candidate.
-//   prologue CTA 0 of the cluster (in the fused CMA-ES mode) samples the
+//   prologue every CTA of the cluster (in the fused CMA-ES mode) samples the
 //            candidate and composes its link transforms in double-float
-//            arithmetic; the other CTAs copy them through distributed shared
-//            memory.
+//            arithmetic (redundantly: no CTA waits for another).
 //   phase 1  every CTA projects its share of the vertices in compensated FP32
 //            (double-float, error-free TwoSum/TwoProd), snapping them to 1/256 px
 //            with round-half-even; the snapped vertices go to an L2-resident
 //            scratch array.
-//   phase 2  after a cluster barrier every CTA takes its share of the
-//            triangles: integer setup (orientation, top-left bias, bbox), then
+//   phase 2  after a cluster barrier the warps of all CTAs take chunks of 32
+//            triangles from a counter in CTA 0's shared memory until none
+//            are left: integer setup (orientation, top-left bias, bbox), then
 //            small triangles are rasterised by one thread each with int32
 //            incremental edge functions, larger ones by a whole warp with
 //            int64 edge functions and __ballot_sync coverage words.  Coverage
@@ -41,75 +41,31 @@ __device__ __forceinline__ dfl dot3(dfl a0, dfl b0, dfl a1, dfl b1, dfl a2, dfl 
     return df_add(df_add(df_mul(a0, b0), df_mul(a1, b1)), df_mul(a2, b2));
 }
 
-// Elementary rotation about x, y or z (identity for TRK_AXIS_NONE).
-static __device__ __noinline__ void rot_elem_df(int axis, dfl a, dfl R[9])
+// Entry (i, j) of the elementary rotation about axis x/y/z (1/2/3; identity
+// for TRK_AXIS_NONE) with sine s and cosine c.
+__device__ __forceinline__ dfl rot_entry(int axis, dfl s, dfl c, int i, int j)
 {
     const dfl one = df_from(1.0f), zero = df_from(0.0f);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) R[i] = (i % 4 == 0) ? one : zero;
-    if (axis == TRK_AXIS_NONE) return;
-    dfl2 sc = df_sincos(a);
-    dfl s = sc.s, c = sc.c;
-    if (axis == TRK_AXIS_X) { R[4] = c; R[5] = df_neg(s); R[7] = s; R[8] = c; }
-    if (axis == TRK_AXIS_Y) { R[0] = c; R[2] = s; R[6] = df_neg(s); R[8] = c; }
-    if (axis == TRK_AXIS_Z) { R[0] = c; R[1] = df_neg(s); R[3] = s; R[4] = c; }
-}
-
-__device__ __forceinline__ void mul3_df(const dfl A[9], const dfl B[9], dfl C[9])
-{
-    dfl T[9];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) T[3 * i + j] = dot3(A[3 * i], B[j], A[3 * i + 1], B[3 + j], A[3 * i + 2], B[6 + j]);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) C[i] = T[i];
-}
-
-// Pose rotation of T_r^c: axis-angle, R = cos(t) I + sin(t) [k]x + (1 - cos(t)) k k^T
-// with t = |r|, k = r / t (I + [r]x when t < 1e-8); or look-at Ry(gamma) Rx(alpha) Rz(beta).
-static __device__ __noinline__ void pose_rotation_df(int rot_param, const float *r, dfl R[9])
-{
-    if (rot_param == TRK_ROT_LOOKAT) {
-        dfl Ry[9], Rx[9], Rz[9], T[9];
-        rot_elem_df(TRK_AXIS_Y, df_from(r[2]), Ry);
-        rot_elem_df(TRK_AXIS_X, df_from(r[0]), Rx);
-        rot_elem_df(TRK_AXIS_Z, df_from(r[1]), Rz);
-        mul3_df(Ry, Rx, T);
-        mul3_df(T, Rz, R);
-        return;
-    }
-    dfl r0 = df_from(r[0]), r1 = df_from(r[1]), r2 = df_from(r[2]);
-    dfl t = df_sqrt(dot3(r0, r0, r1, r1, r2, r2));
-    const dfl one = df_from(1.0f);
-    if (t.hi < 1e-8f) {
-        R[0] = one; R[1] = df_neg(r2); R[2] = r1;
-        R[3] = r2; R[4] = one; R[5] = df_neg(r0);
-        R[6] = df_neg(r1); R[7] = r0; R[8] = one;
-        return;
-    }
-    dfl it = df_div(df_from(1.0f), t);
-    dfl k[3] = {df_mul(r0, it), df_mul(r1, it), df_mul(r2, it)};
-    dfl2 sc = df_sincos(t);
-    dfl s = sc.s, c = sc.c;
-    dfl c1 = df_sub(one, c);
-    dfl Kx[9] = {df_from(0.f), df_neg(k[2]), k[1], k[2], df_from(0.f), df_neg(k[0]), df_neg(k[1]), k[0], df_from(0.f)};
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            dfl v = df_fma(c1, df_mul(k[i], k[j]), df_mul(s, Kx[3 * i + j]));
-            R[3 * i + j] = (i == j) ? df_add(v, c) : v;
-        }
+    if (axis == TRK_AXIS_NONE) return i == j ? one : zero;
+    const int a = axis - 1;  // the fixed coordinate
+    if (i == a || j == a) return i == j ? one : zero;
+    if (i == j) return c;
+    // x: (1,2) = -s, (2,1) = s; y: (0,2) = s, (2,0) = -s; z: (0,1) = -s, (1,0) = s
+    const bool neg = (axis == TRK_AXIS_Y) ? (i > j) : (i < j);
+    return neg ? df_neg(s) : s;
 }
 
 // Projective rows of every frame for one instrument state, computed by one
 // warp in double-float: rows (fx M0, fy M1, M2) of M = T_r^c T_f(q) with
 // T_f = T_parent * [Rot(axis_f, coef_f q_joint) | offset_f] and q from the
 // inverse cosine map q = lb + (ub-lb)/2 (1 - cos(pi (qh-lb)/(ub-lb))),
-// written as hi/lo float pairs (24 floats per frame).  Lanes work on
-// independent pieces (joint maps, pose rotation, joint rotations, matrix
-// entries).  scr: kComposeScratch float2.
+// written as hi/lo float pairs (24 floats per frame).  The pose rotation is
+// axis-angle, R = cos t I + sin t [k]x + (1 - cos t) k k^T with t = |r|,
+// k = r / t (I + [r]x when t < 1e-8), or look-at Ry(gamma) Rx(alpha) Rz(beta)
+// (Sec. III-A.3).  The lanes run the same code on different data: one
+// sine/cosine evaluation gives the three joint maps and the pose angles,
+// a second one the joint rotations, then the chain products.
+// scr: kComposeScratch float2.
 constexpr int kComposeScratch = 3 + 9 + kMaxFrames * 9 + kMaxFrames * 12;
 
 __device__ void compose_frames_warp(const ChainDev &ch, const CamDev &cam, const float *st, float *out,
@@ -117,25 +73,78 @@ __device__ void compose_frames_warp(const ChainDev &ch, const CamDev &cam, const
 {
     float2 *qs = scr, *Rs = scr + 3, *Js = scr + 12, *Ts = scr + 12 + kMaxFrames * 9;
     const int nF = ch.n_frames;
+    const bool lookat = ch.rot_param == TRK_ROT_LOOKAT;
+    const dfl r0 = df_from(st[0]), r1 = df_from(st[1]), r2 = df_from(st[2]);
+    const dfl t = lookat ? df_from(0.0f) : df_sqrt(dot3(r0, r0, r1, r1, r2, r2));
+    // step 1: lanes 0-2 the joint maps' angles, lane 3 the pose angle t (or
+    // the look-at angles gamma, alpha, beta on lanes 3-5)
+    dfl arg = df_from(0.0f);
+    if (lane < 3)
+        arg = df_mul(df_sub(df_from(st[6 + lane]), dfc(ch.lb_df[lane])), dfc(ch.pi_over_range_df[lane]));
+    else if (lane == 3)
+        arg = lookat ? r2 : t;
+    else if (lane == 4 && lookat)
+        arg = r0;
+    else if (lane == 5 && lookat)
+        arg = r1;
+    const dfl2 sc = df_sincos(arg);
     if (lane < 3) {
-        dfl arg = df_mul(df_sub(df_from(st[6 + lane]), dfc(ch.lb_df[lane])), dfc(ch.pi_over_range_df[lane]));
-        dfl cs = df_sincos(arg).c;
-        dfl q = df_fma(dfc(ch.half_range_df[lane]), df_sub(df_from(1.0f), cs), dfc(ch.lb_df[lane]));
+        const dfl q = df_fma(dfc(ch.half_range_df[lane]), df_sub(df_from(1.0f), sc.c), dfc(ch.lb_df[lane]));
         qs[lane] = make_float2(q.hi, q.lo);
-    }
-    if (lane == 3) {
-        dfl R[9];
-        pose_rotation_df(ch.rot_param, st, R);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) Rs[i] = make_float2(R[i].hi, R[i].lo);
+    } else if (lane < 6) {  // pose sines and cosines, parked in the chain scratch
+        Ts[2 * (lane - 3)] = make_float2(sc.s.hi, sc.s.lo);
+        Ts[2 * (lane - 3) + 1] = make_float2(sc.c.hi, sc.c.lo);
     }
     __syncwarp();
-    if (lane < nF) {
-        dfl J[9];
-        rot_elem_df(ch.axis[lane], df_mul(dfc(ch.coef_df[lane]), dfc(qs[ch.joint[lane]])), J);
+    // step 2: joint rotations (lanes < nF) and the pose rotation (lanes 0-8)
+    dfl ang = df_from(0.0f);
+    if (lane < nF) ang = df_mul(dfc(ch.coef_df[lane]), dfc(qs[ch.joint[lane]]));
+    const dfl2 fsc = df_sincos(ang);
+    dfl Rv = df_from(0.0f);
+    if (lane < 9) {
+        const int i = lane / 3, j = lane - 3 * (lane / 3);
+        if (lookat) {
+            const dfl sg = dfc(Ts[0]), cg = dfc(Ts[1]), sa = dfc(Ts[2]), ca = dfc(Ts[3]), sb = dfc(Ts[4]),
+                      cb = dfc(Ts[5]);
+            dfl row[3];  // row i of Ry(gamma) Rx(alpha)
 #pragma unroll
-        for (int i = 0; i < 9; ++i) Js[9 * lane + i] = make_float2(J[i].hi, J[i].lo);
+            for (int l = 0; l < 3; ++l)
+                row[l] = dot3(rot_entry(TRK_AXIS_Y, sg, cg, i, 0), rot_entry(TRK_AXIS_X, sa, ca, 0, l),
+                              rot_entry(TRK_AXIS_Y, sg, cg, i, 1), rot_entry(TRK_AXIS_X, sa, ca, 1, l),
+                              rot_entry(TRK_AXIS_Y, sg, cg, i, 2), rot_entry(TRK_AXIS_X, sa, ca, 2, l));
+            Rv = dot3(row[0], rot_entry(TRK_AXIS_Z, sb, cb, 0, j), row[1], rot_entry(TRK_AXIS_Z, sb, cb, 1, j),
+                      row[2], rot_entry(TRK_AXIS_Z, sb, cb, 2, j));
+        } else {
+            const dfl r[3] = {r0, r1, r2};
+            if (t.hi < 1e-8f) {
+                // I + [r]x: (0,1) = -r2, (0,2) = r1, (1,0) = r2, (1,2) = -r0, (2,0) = -r1, (2,1) = r0
+                const int m = 3 - i - j;
+                const bool neg = ((i + 1) % 3) == j;
+                Rv = i == j ? df_from(1.0f) : (neg ? df_neg(r[m]) : r[m]);
+            } else {
+                const dfl it = df_div(df_from(1.0f), t);
+                const dfl s = dfc(Ts[0]), c = dfc(Ts[1]);
+                const dfl ki = df_mul(r[i], it), kj = df_mul(r[j], it);
+                dfl Kij = df_from(0.0f);
+                if (i != j) {
+                    const int m = 3 - i - j;
+                    const bool neg = ((i + 1) % 3) == j;
+                    const dfl km = df_mul(r[m], it);
+                    Kij = neg ? df_neg(km) : km;
+                }
+                Rv = df_fma(df_sub(df_from(1.0f), c), df_mul(ki, kj), df_mul(s, Kij));
+                if (i == j) Rv = df_add(Rv, c);
+            }
+        }
     }
+    if (lane < nF) {
+#pragma unroll
+        for (int e = 0; e < 9; ++e) {
+            const dfl v = rot_entry(ch.axis[lane], fsc.s, fsc.c, e / 3, e % 3);
+            Js[9 * lane + e] = make_float2(v.hi, v.lo);
+        }
+    }
+    if (lane < 9) Rs[lane] = make_float2(Rv.hi, Rv.lo);
     __syncwarp();
     for (int f = 0; f < nF; ++f) {  // parents first; lane = 4 i + j
         if (lane < 12) {
@@ -417,25 +426,24 @@ __device__ __forceinline__ void eval_candidate(const EvalArgs &a, int c, const u
 
     for (int w = tid; w < nwords; w += nthr) bm[w] = 0u;
     if (tid < 8) sacc[tid] = 0;
-    // ---- prologue: CTA 0 of the cluster samples (fused CMA-ES mode) and
-    //      composes the candidate's frames in FP64; the others copy them ----
-    if (rank == 0) {
+    // ---- prologue: every CTA samples the candidate (fused CMA-ES mode; the
+    //      draws are the same in every CTA and CTA 0 stores them) and composes
+    //      its frames in double-float, so no CTA waits for another ----
+    {
         const float *par = a.params + (size_t)c * a.d;
         if (a.cma_st) {
-            if (warp == 0)
-                cma_sample_warp(*a.cma_k, a.cma_st, c, nullptr, a.cma_y, a.cma_z, const_cast<float *>(a.params),
-                                s_par, s_z, lane);
+            if (warp == 0) {
+                const bool owner = rank == 0;
+                cma_sample_warp(*a.cma_k, a.cma_st, c, nullptr, owner ? a.cma_y : nullptr,
+                                owner ? a.cma_z : nullptr, owner ? const_cast<float *>(a.params) : nullptr, s_par,
+                                s_z, lane);
+            }
             __syncthreads();
             par = s_par;
         }
         if (warp < nI)
             compose_frames_warp(a.ch, a.cam, par + 9 * warp, sM + warp * nF * 24, scr + warp * kComposeScratch,
                                 lane);
-    }
-    cluster.sync();
-    if (rank != 0) {
-        const float *src = cluster.map_shared_rank(sM, 0);
-        for (int e = tid; e < nI * nF * 24; e += nthr) sM[e] = src[e];
     }
     __syncthreads();
 
@@ -463,62 +471,81 @@ __device__ __forceinline__ void eval_candidate(const EvalArgs &a, int c, const u
     }
     cluster.sync();  // arrive.release / wait.acquire: the snapped vertices are visible cluster-wide
 
-    // ---- phase 2: triangles -> this CTA's bitmap, next triangle's loads in flight ----
+    // ---- phase 2: triangles -> this CTA's bitmap.  Warps of the whole cluster
+    //      take chunks of 32 triangles (one per lane) from a counter in CTA 0's
+    //      shared memory, so the cluster finishes together whatever the
+    //      triangles cost; the bitmaps are OR-ed in phase 3, so which CTA draws a
+    //      triangle does not change the result.  Three chunks are in flight:
+    //      the next chunk's vertices, the one after's indices and a ticket ----
     int culled = 0;
     const int NT = nI * a.T;
     {
-        int tt = gtid;
-        int4 tri_c = make_int4(0, 0, 0, 0), tri_n = make_int4(0, 0, 0, 0);
-        int bc = 0, bn = 0;
+        int *ctr = cluster.map_shared_rank(&sacc[5], 0);
+        auto ticket = [&]() {
+            int v = 0;
+            if (lane == 0) v = atomicAdd(ctr, 1);
+            return __shfl_sync(0xffffffffu, v, 0);
+        };
+        // chunk being drawn (vertices loaded), next chunk (indices loaded), and
+        // the one after (ticket taken)
+        int cur = ticket(), nx1 = ticket(), nx2 = ticket();
+        int t0 = cur * 32 + lane, t1 = nx1 * 32 + lane;
+        int4 tri1 = make_int4(0, 0, 0, 0);
+        int b1 = 0;
         int2 v0 = make_int2(0, 0), v1 = v0, v2 = v0;
-        if (tt < NT) {
-            bc = tt >= a.T;  // instrument (at most 2): no division
-            tri_c = a.tris[tt - bc * a.T];
-            const int2 *sv = snapc + bc * a.V;
+        if (t0 < NT) {
+            const int b0 = t0 >= a.T;  // instrument (at most 2): no division
+            const int4 tri0 = a.tris[t0 - b0 * a.T];
+            const int2 *sv = snapc + b0 * a.V;
             // written by other CTAs of the cluster in phase 1: read through L2
-            v0 = __ldcg(sv + tri_c.x);
-            v1 = __ldcg(sv + tri_c.y);
-            v2 = __ldcg(sv + tri_c.z);
+            v0 = __ldcg(sv + tri0.x);
+            v1 = __ldcg(sv + tri0.y);
+            v2 = __ldcg(sv + tri0.z);
         }
-        int tn = tt + gstride;
-        if (tn < NT) {
-            bn = tn >= a.T;
-            tri_n = a.tris[tn - bn * a.T];
+        if (t1 < NT) {
+            b1 = t1 >= a.T;
+            tri1 = a.tris[t1 - b1 * a.T];
         }
-        while (tt < NT) {
-            const int tnn = tn + gstride;
+        while (cur * 32 < NT) {  // tickets of one warp increase: once past the end, done
+            const int nx3 = ticket();
             int2 w0 = make_int2(0, 0), w1 = w0, w2 = w0;
-            int4 tri_nn = make_int4(0, 0, 0, 0);
-            int bnn = 0;
-            if (tn < NT) {
-                const int2 *svn = snapc + bn * a.V;
-                w0 = __ldcg(svn + tri_n.x);
-                w1 = __ldcg(svn + tri_n.y);
-                w2 = __ldcg(svn + tri_n.z);
+            if (t1 < NT) {
+                const int2 *svn = snapc + b1 * a.V;
+                w0 = __ldcg(svn + tri1.x);
+                w1 = __ldcg(svn + tri1.y);
+                w2 = __ldcg(svn + tri1.z);
             }
-            if (tnn < NT) {
-                bnn = tnn >= a.T;
-                tri_nn = a.tris[tnn - bnn * a.T];
+            const int t2 = nx2 * 32 + lane;
+            int4 tri2 = make_int4(0, 0, 0, 0);
+            int b2 = 0;
+            if (t2 < NT) {
+                b2 = t2 >= a.T;
+                tri2 = a.tris[t2 - b2 * a.T];
             }
-            TriSetup t;
-            int st = tri_setup(v0, v1, v2, W, H, a.cull, t);
-            if (st == 2) ++culled;
-            if (st == 1) {
-                if (t.spanx < 32 * 256 && t.spany < 64 * 256) {
-                    raster_small(t, bm, Wq);
-                } else {
-                    int slot = atomicAdd(&sacc[4], 1);
-                    if (slot < kBigListCap) big[slot] = tt;
-                    else raster_serial(t, bm, Wq);
+            if (t0 < NT) {
+                TriSetup t;
+                const int st = tri_setup(v0, v1, v2, W, H, a.cull, t);
+                if (st == 2) ++culled;
+                if (st == 1) {
+                    if (t.spanx < 32 * 256 && t.spany < 64 * 256) {
+                        raster_small(t, bm, Wq);
+                    } else {
+                        int slot = atomicAdd(&sacc[4], 1);
+                        if (slot < kBigListCap) big[slot] = t0;
+                        else raster_serial(t, bm, Wq);
+                    }
                 }
             }
-            tt = tn;
-            tn = tnn;
+            cur = nx1;
+            t0 = t1;
             v0 = w0;
             v1 = w1;
             v2 = w2;
-            tri_n = tri_nn;
-            bn = bnn;
+            nx1 = nx2;
+            t1 = t2;
+            tri1 = tri2;
+            b1 = b2;
+            nx2 = nx3;
         }
     }
     __syncthreads();
