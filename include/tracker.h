@@ -286,6 +286,34 @@ trk_status track_frame_host(trk_cmaes *es, const uint8_t *mask_host, int32_t gen
                             const float *joint_reading_host, float *pose_out_host, float *best_loss_out,
                             void *stream);
 
+/* Keypoint term of the objective (Eq. kpts_loss): L = L_render + lambda_kpts
+ * sum over instruments of L_kpts, with L_kpts = min over the two assignments
+ * of sum_i (|t_i^r - t_sigma(i)^p| - tau)_+ + (|t_mean^r - t_mean^p| - tau)_+,
+ * t^p the candidate's projected keypoints (px, image coordinates) and t^r the
+ * detections.  The keypoints are two points (mm) in kinematic frames
+ * frame[0], frame[1] (the jaw tips).  The term is evaluated for an instrument
+ * only when its detection is valid (the paper's "exactly two keypoints").
+ * Default: lambda_kpts = 0 (off).  Synchronous, host-side settings. */
+typedef struct {
+    int32_t frame[2];
+    double point[2][3];
+    double tau;          /* px */
+    double lambda_kpts;  /* weight in loss units per px */
+} trk_keypoints;
+trk_status tracker_set_keypoints(trk_tracker *t, const trk_keypoints *kp);
+
+/* Detections for the following launches: obs_dev [n_instruments * 5] floats
+ * (x1, y1, x2, y2, valid) per instrument, device memory owned by the caller
+ * and read by every later fitness launch of this tracker (update its contents
+ * on the launching stream between frames); NULL turns the term off.  Batches
+ * and servers take the pointer when they are created. */
+trk_status tracker_set_keypoint_obs(trk_tracker *t, const float *obs_dev);
+
+/* Projected keypoints of n states [n*d] (device): out_dev [n * n_inst * 4]
+ * = (u1, v1, u2, v2) per instrument, image coordinates.  Asynchronous. */
+trk_status tracker_project_keypoints(trk_tracker *t, const float *states_dev, int32_t n, float *out_dev,
+                                     void *stream);
+
 /* ---------------------------------------------------------------------------
  * Soft (differentiable) silhouette.  The paper fits with a differentiable
  * renderer (Sec. III-A.2) and the MSE term of Eq. (render_loss); this is the
@@ -445,6 +473,28 @@ trk_status server_poll(trk_server *v, trk_frame_result *out, int32_t max_out, in
  * staging buffers (any output may be NULL). */
 trk_status server_stats(const trk_server *v, int64_t *ticks, int32_t *n_active, int32_t *n_queued,
                         int32_t *free_staging);
+
+/* Temporal filter (Sec. III-A, temporal filtering): a constant-velocity
+ * Kalman filter on the frame estimates, state (Theta, dTheta/dt) with the joint
+ * coordinates as joint angles q.  Process noise is block-diagonal with one
+ * 2x2 block diag(q_pos[i], q_vel[i]) per coordinate, measurement noise
+ * diagonal r[i], so the filter runs as one (position, velocity) filter per
+ * coordinate.  The first frame initialises s = (z, 0), P = diag(r, p_vel0);
+ * every later frame predicts at its reset (s <- F s, P <- F P F^T + Q with
+ * F = [[1, dt], [0, 1]]) and updates with the frame's best candidate as the
+ * measurement.  The filtered state, joint angles clamped to their limits, is
+ * the frame's estimate and pose output; with seed_mean != 0 the prediction
+ * (rather than the last estimate) is the next frame's search mean.  Joint
+ * readings, when given, still replace the joints of the mean.  Units: rad,
+ * mm, rad of joint angle; dt in the caller's time unit.  Arrays have d
+ * entries (up to TRK_MAX_D).  Setting the filter clears its state.
+ * Synchronises `stream`. */
+typedef struct {
+    int32_t enabled, seed_mean;
+    double dt;
+    double q_pos[TRK_MAX_D], q_vel[TRK_MAX_D], r[TRK_MAX_D], p_vel0[TRK_MAX_D];
+} trk_filter;
+trk_status cmaes_set_filter(trk_cmaes *es, const trk_filter *f, void *stream);
 
 /* Checkpoint: the whole optimiser state as a plain blob.  cmaes_save with
  * blob = NULL sets *n to the size needed.  A loaded optimiser continues

@@ -51,6 +51,17 @@ class Config(C.Structure):
                 ("lambda_max", C.c_int32), ("cluster", C.c_int32), ("block_threads", C.c_int32)]
 
 
+class Keypoints(C.Structure):
+    _fields_ = [("frame", C.c_int32 * 2), ("point", (C.c_double * 3) * 2), ("tau", C.c_double),
+                ("lambda_kpts", C.c_double)]
+
+
+class Filter(C.Structure):
+    _fields_ = [("enabled", C.c_int32), ("seed_mean", C.c_int32), ("dt", C.c_double),
+                ("q_pos", C.c_double * TRK_MAX_D), ("q_vel", C.c_double * TRK_MAX_D), ("r", C.c_double * TRK_MAX_D),
+                ("p_vel0", C.c_double * TRK_MAX_D)]
+
+
 class FrameResult(C.Structure):
     _fields_ = [("tag", C.c_uint64), ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
                 ("stream", C.c_int32), ("d", C.c_int32), ("pose", C.c_float * TRK_MAX_D), ("best_loss", C.c_float),
@@ -92,6 +103,10 @@ SIGNATURES = {
     "batch_track_frame": [P, P, I32, P, I32, P],
     "batch_autotune": [P, P, P, I32, P, P, P, P],
     "soft_eval": [P, P, I32, P, C.c_float, P, P, P],
+    "cmaes_set_filter": [P, P, P],
+    "tracker_set_keypoints": [P, P],
+    "tracker_set_keypoint_obs": [P, P],
+    "tracker_project_keypoints": [P, P, I32, P, P],
     "soft_refine": [P, P, I32, I32, C.c_float, C.c_float, P, P, P],
     "server_create": [I32, I32, I32, C.c_int64, I32, C.c_int64, I32, I32, P],
     "server_destroy": [P],

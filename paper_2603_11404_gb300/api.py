@@ -140,6 +140,31 @@ class Tracker:
              _ptr(snap), _ptr(uv), _stream(stream))
         return loss, counts, snap, uv
 
+    def set_keypoints(self, frames, points, tau: float, lambda_kpts: float):
+        """tracker_set_keypoints: two keypoints (frame index, point in mm in that frame)."""
+        kp = _abi.Keypoints()
+        for k in range(2):
+            kp.frame[k] = int(frames[k])
+            for j in range(3):
+                kp.point[k][j] = float(points[k][j])
+        kp.tau, kp.lambda_kpts = float(tau), float(lambda_kpts)
+        call("tracker_set_keypoints", self.h, C.byref(kp))
+
+    def set_keypoint_obs(self, obs: torch.Tensor | None):
+        """tracker_set_keypoint_obs: device tensor [n_inst, 5] (x1, y1, x2, y2, valid) or None."""
+        if obs is not None:
+            _check_dev(obs, torch.float32, "obs")
+        self._kp_obs = obs
+        call("tracker_set_keypoint_obs", self.h, _ptr(obs))
+
+    def project_keypoints(self, states: torch.Tensor, stream=None) -> torch.Tensor:
+        """tracker_project_keypoints: [n, d] states -> [n, n_inst, 4] (u1, v1, u2, v2)."""
+        _check_dev(states, torch.float32, "states")
+        n = states.shape[0]
+        out = torch.empty((n, self.scene.n_instruments, 4), dtype=torch.float32, device=states.device)
+        call("tracker_project_keypoints", self.h, _ptr(states), n, _ptr(out), _stream(stream))
+        return out
+
     def soft_eval(self, params: torch.Tensor, mask_packed: torch.Tensor, sigma: float = 1.0, grad: bool = False,
                   stream=None):
         """soft_eval: soft-silhouette loss [lam] (and dL/dparams [lam, d] when grad)."""
@@ -257,6 +282,20 @@ class CMAES:
         call("track_frame_host", self.h, _ptr(mask_u8), int(generations), _ptr(jr), _ptr(pose), C.byref(bl),
              _stream(stream))
         return pose, bl.value
+
+    def set_filter(self, dt: float, q_pos, q_vel, r, p_vel0=None, seed_mean: bool = True, enabled: bool = True,
+                   stream=None):
+        """cmaes_set_filter: constant-velocity Kalman filter on the frame estimates
+        (per-coordinate arrays, or scalars broadcast to all d coordinates)."""
+        f = _abi.Filter()
+        f.enabled, f.seed_mean, f.dt = int(bool(enabled)), int(bool(seed_mean)), float(dt)
+        arrs = [np.broadcast_to(np.asarray(x, np.float64), (self.d,)) for x in
+                (q_pos, q_vel, r, np.full(self.d, 1e2) if p_vel0 is None else p_vel0)]
+        for name, a in zip(("q_pos", "q_vel", "r", "p_vel0"), arrs):
+            dst = getattr(f, name)
+            for i in range(self.d):
+                dst[i] = float(a[i])
+        call("cmaes_set_filter", self.h, C.byref(f), _stream(stream))
 
     def refine(self, mask_packed: torch.Tensor, top_k: int = 8, steps: int = 10, lr: float = 0.05,
                sigma: float = 1.0, pose_out: torch.Tensor | None = None, stream=None):

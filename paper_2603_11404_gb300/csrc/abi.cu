@@ -232,6 +232,43 @@ trk_status tracker_create(const trk_link_mesh *meshes, int32_t n_meshes, const t
     return TRK_OK;
 }
 
+trk_status tracker_set_keypoints(trk_tracker *t, const trk_keypoints *kp)
+{
+    if (!t || !kp) return inval("NULL argument");
+    for (int k = 0; k < 2; ++k)
+        if (kp->frame[k] < 0 || kp->frame[k] >= t->ch.n_frames) return inval("keypoint frame out of range");
+    if (!(kp->tau >= 0.0) || !(kp->lambda_kpts >= 0.0)) return inval("tau and lambda_kpts must be >= 0");
+    for (int k = 0; k < 2; ++k) {
+        t->kp_frame[k] = kp->frame[k];
+        for (int j = 0; j < 3; ++j) t->kp_pt[k][j] = (float)kp->point[k][j];
+    }
+    t->kp_tau = (float)kp->tau;
+    t->kp_lambda = (float)kp->lambda_kpts;
+    return TRK_OK;
+}
+
+trk_status tracker_set_keypoint_obs(trk_tracker *t, const float *obs_dev)
+{
+    if (!t) return inval("NULL tracker");
+    t->kp_obs = obs_dev;
+    return TRK_OK;
+}
+
+trk_status tracker_project_keypoints(trk_tracker *t, const float *states_dev, int32_t n, float *out_dev, void *stream)
+{
+    if (!t) return inval("NULL tracker");
+    if (n < 0) return inval("n < 0");
+    if (n == 0) return TRK_OK;
+    if (!states_dev || !out_dev) return inval("NULL device pointer");
+    EvalArgs a{};
+    a.ch = t->ch;
+    a.cam = t->cam;
+    a.d = t->d;
+    apply_keypoints(a, t);
+    CU(launch_project_keypoints(a, states_dev, n, out_dev, as_stream(stream)), "project keypoints");
+    return TRK_OK;
+}
+
 trk_status tracker_destroy(trk_tracker *t)
 {
     if (!t) return inval("NULL tracker");
@@ -286,6 +323,7 @@ static trk_status eval_impl(trk_tracker *t, const float *params, int32_t lam, co
     a.loss_kind = t->cfg.loss_kind;
     a.lambda_app = t->cfg.lambda_app;
     a.cull = t->cfg.cull_backfaces;
+    apply_keypoints(a, t);
     CU(launch_eval(a, t->lc, as_stream(stream)), "eval_population launch");
     return TRK_OK;
 }
@@ -432,6 +470,35 @@ trk_status cmaes_create(trk_tracker *t, int32_t lam, const double *mean_host, co
     return TRK_OK;
 }
 
+trk_status cmaes_set_filter(trk_cmaes *es, const trk_filter *f, void *stream)
+{
+    if (!es || !f) return inval("NULL argument");
+    const int d = es->d;
+    if (f->enabled) {
+        if (!(f->dt > 0.0)) return inval("filter dt must be > 0");
+        for (int i = 0; i < d; ++i)
+            if (!(f->q_pos[i] >= 0.0) || !(f->q_vel[i] >= 0.0) || !(f->r[i] > 0.0) || !(f->p_vel0[i] >= 0.0))
+                return inval("filter noise: q_pos, q_vel, p_vel0 >= 0 and r > 0 required");
+    }
+    KfConst &c = es->hk.kf;
+    c = KfConst{};
+    c.enabled = f->enabled ? 1 : 0;
+    c.seed_mean = f->seed_mean ? 1 : 0;
+    c.dt = f->dt;
+    for (int i = 0; i < d; ++i) {
+        c.q_pos[i] = f->q_pos[i];
+        c.q_vel[i] = f->q_vel[i];
+        c.r[i] = f->r[i];
+        c.p_vel0[i] = f->p_vel0[i];
+    }
+    cudaStream_t s = as_stream(stream);
+    const int zero = 0;
+    CU(cudaMemcpyAsync(es->k, &es->hk, sizeof(CmaConst), cudaMemcpyHostToDevice, s), "filter upload");
+    CU(cudaMemcpyAsync(&es->st->kf.initialized, &zero, sizeof(int), cudaMemcpyHostToDevice, s), "filter reset");
+    CU(cudaStreamSynchronize(s), "filter upload sync");
+    return TRK_OK;
+}
+
 trk_status cmaes_destroy(trk_cmaes *es)
 {
     if (!es) return inval("NULL optimiser");
@@ -514,6 +581,7 @@ static trk_status fused_generation(trk_cmaes *es, const uint32_t *mask, int fini
     a.loss_kind = t->cfg.loss_kind;
     a.lambda_app = t->cfg.lambda_app;
     a.cull = t->cfg.cull_backfaces;
+    apply_keypoints(a, t);
     a.cma_k = es->k;
     a.cma_st = es->st;
     a.cma_y = es->y;
@@ -614,7 +682,7 @@ trk_status cmaes_save(trk_cmaes *es, void *blob, size_t *n, void *stream)
         return TRK_OK;
     }
     if (*n < need) return inval("blob too small");
-    BlobHeader h{kBlobMagic, 1u, (uint32_t)es->d, (uint32_t)es->lam, (uint32_t)sizeof(CmaState), 0u};
+    BlobHeader h{kBlobMagic, 2u, (uint32_t)es->d, (uint32_t)es->lam, (uint32_t)sizeof(CmaState), 0u};
     memcpy(blob, &h, sizeof h);
     CU(cudaMemcpyAsync((char *)blob + sizeof h, es->st, sizeof(CmaState), cudaMemcpyDeviceToHost, as_stream(stream)),
        "save copy");
@@ -629,7 +697,7 @@ trk_status cmaes_load(trk_cmaes *es, const void *blob, size_t n, void *stream)
     if (n < sizeof(BlobHeader) + sizeof(CmaState)) return inval("blob too small");
     BlobHeader h;
     memcpy(&h, blob, sizeof h);
-    if (h.magic != kBlobMagic || h.version != 1u || h.d != (uint32_t)es->d || h.lam != (uint32_t)es->lam ||
+    if (h.magic != kBlobMagic || h.version != 2u || h.d != (uint32_t)es->d || h.lam != (uint32_t)es->lam ||
         h.state_bytes != sizeof(CmaState))
         return inval("blob does not match this optimiser");
     CU(cudaMemcpyAsync(es->st, (const char *)blob + sizeof h, sizeof(CmaState), cudaMemcpyHostToDevice,

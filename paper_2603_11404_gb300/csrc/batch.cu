@@ -177,6 +177,7 @@ trk_status batch_create(trk_tracker *const *trackers, trk_cmaes *const *optimise
         a.loss_kind = t->cfg.loss_kind;
         a.lambda_app = t->cfg.lambda_app;
         a.cull = t->cfg.cull_backfaces;
+        apply_keypoints(a, t);
         off += (long long)b->lam[i] * t->ch.n_inst * std::max(t->V, 1);
         if (trk_cmaes *es = b->es[i]) {
             a.params = es->params;

@@ -523,13 +523,78 @@ static __device__ __noinline__ void cma_tell_block(const CmaConst &k, CmaState *
 }
 
 // Frame epilogue: the frame's best candidate becomes the estimate.
+// Joint angle from the unconstrained coordinate (Sec. III-A.3, inverse map).
+__device__ __forceinline__ double q_from_qhat(double qh, double lb, double ub)
+{
+    if (ub == lb) return lb;
+    return lb + 0.5 * (ub - lb) * (1.0 - cos(M_PI * (qh - lb) / (ub - lb)));
+}
+
+// Is state coordinate i a joint, and which one (0..2)?
+__device__ __forceinline__ int joint_of(int i) { const int r = i % 9; return r >= 6 ? r - 6 : -1; }
+
+// Kalman prediction s <- F s, P <- F P F^T + Q (F = [[1, dt], [0, 1]] per coordinate).
+__device__ __forceinline__ void kf_predict(const KfConst &c, KfState &f, int i)
+{
+    const double dt = c.dt;
+    double *s = f.s[i], *P = f.P[i];
+    s[0] += dt * s[1];
+    const double p00 = P[0] + 2.0 * dt * P[1] + dt * dt * P[2] + c.q_pos[i];
+    const double p01 = P[1] + dt * P[2];
+    P[0] = p00;
+    P[1] = p01;
+    P[2] = P[2] + c.q_vel[i];
+}
+
+// The filter's position of coordinate i back in state units (joint angles
+// clamped to their limits, then mapped to the unconstrained coordinate).
+__device__ __forceinline__ double kf_to_state(const CmaConst &k, const KfState &f, int i)
+{
+    const int j = joint_of(i);
+    const double x = f.s[i][0];
+    if (j < 0) return x;
+    const double q = fmin(k.q_ub[j], fmax(k.q_lb[j], x));
+    return qhat_from_q(q, k.q_lb[j], k.q_ub[j]);
+}
+
+// Frame epilogue: the frame's best candidate becomes the estimate; with the
+// filter on it is the measurement z_t of the Kalman update (joints as angles)
+// and the filtered state becomes the estimate.
 __device__ __forceinline__ void cma_finish_frame(const CmaConst &k, CmaState *st, float *pose_out, int tid, int nt)
 {
+    const bool kf = k.kf.enabled != 0;
+    const bool first = kf && !st->kf.initialized;
     for (int i = tid; i < k.d; i += nt) {
-        float b = st->best_x[i];
-        st->est[i] = (double)b;
-        if (pose_out) pose_out[i] = b;
+        const float b = st->best_x[i];
+        double e = (double)b;
+        if (kf) {
+            const int j = joint_of(i);
+            const double z = j < 0 ? e : q_from_qhat(e, k.q_lb[j], k.q_ub[j]);
+            KfState &f = st->kf;
+            double *s = f.s[i], *P = f.P[i];
+            if (first) {
+                s[0] = z;
+                s[1] = 0.0;
+                P[0] = k.kf.r[i];
+                P[1] = 0.0;
+                P[2] = k.kf.p_vel0[i];
+            } else {  // gain K = P H^T / (H P H^T + r), H = [1 0]
+                const double S = P[0] + k.kf.r[i];
+                const double k0 = P[0] / S, k1 = P[1] / S, y = z - s[0];
+                s[0] += k0 * y;
+                s[1] += k1 * y;
+                const double p00 = (1.0 - k0) * P[0], p01 = (1.0 - k0) * P[1], p11 = P[2] - k1 * P[1];
+                P[0] = p00;
+                P[1] = p01;
+                P[2] = p11;
+            }
+            e = kf_to_state(k, f, i);
+        }
+        st->est[i] = e;
+        if (pose_out) pose_out[i] = kf ? (float)e : b;
     }
+    __syncthreads();
+    if (first && tid == 0) st->kf.initialized = 1;
 }
 
 }  // namespace trk

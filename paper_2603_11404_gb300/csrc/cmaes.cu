@@ -10,8 +10,14 @@ __device__ void cma_reset_body(const CmaConst &k, CmaState *st, const double *me
                                const float *joint_reading, int n_inst, int tid, int nt)
 {
     const int d = k.d;
+    // a new frame: the Kalman prediction, whose position seeds the mean if asked to
+    const bool predict = from_est && k.kf.enabled && st->kf.initialized;
     for (int i = tid; i < d; i += nt) {
         double mi = from_est ? st->est[i] : mean_dev[i];
+        if (predict) {
+            kf_predict(k.kf, st->kf, i);
+            if (k.kf.seed_mean) mi = kf_to_state(k, st->kf, i);
+        }
         int b = i / 9, r = i - 9 * b;
         if (joint_reading && r >= 6 && b < n_inst)
             mi = qhat_from_q((double)joint_reading[3 * b + (r - 6)], k.q_lb[r - 6], k.q_ub[r - 6]);

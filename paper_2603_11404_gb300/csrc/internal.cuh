@@ -66,12 +66,35 @@ struct __align__(16) EvalArgs {
     unsigned *cma_done;        // CTA ticket counter, zero between launches
     float *cma_pose_out;       // frame estimate output (finish only), may be NULL
     int cma_finish;            // 1: also make the frame's best the estimate
+    // keypoint term of the objective (Eq. kpts_loss): two keypoints per
+    // instrument (frame, point in that frame), threshold tau, weight lambda;
+    // kp_obs [n_inst * 5] = detected (x1, y1, x2, y2, valid) or NULL (term off)
+    int kp_frame[2];
+    float kp_pt[2][3];
+    float kp_tau, kp_lambda;
+    const float *kp_obs;
 };
 
 struct LaunchCfg {
     int cluster;           // CTAs per candidate
     int threads;           // threads per CTA
     size_t smem;           // dynamic shared memory per CTA
+};
+
+// Constant-velocity Kalman filter on the frame estimates (temporal filtering,
+// Sec. III-A): state (Theta, dTheta/dt) with the joint coordinates as joint
+// angles q; process noise block-diagonal, one 2x2 block diag(q_pos, q_vel)
+// per coordinate, measurement noise diagonal, so the filter splits into one
+// (position, velocity) filter per coordinate.
+struct KfConst {
+    int enabled, seed_mean;  // seed_mean: the prediction is the next frame's mean
+    double dt;
+    double q_pos[kMaxD], q_vel[kMaxD], r[kMaxD], p_vel0[kMaxD];
+};
+struct KfState {
+    int initialized, pad;
+    double s[kMaxD][2];      // position, velocity
+    double P[kMaxD][3];      // covariance p00, p01, p11
 };
 
 // CMA-ES constants, host-computed in FP64 (Hansen's tutorial defaults).
@@ -87,6 +110,7 @@ struct CmaConst {
     double q_lb[3], q_ub[3];
     unsigned long long seed;
     unsigned stream_id;
+    KfConst kf;
 };
 
 // Device-resident CMA-ES state (FP64 except the FP32 population and best).
@@ -105,6 +129,7 @@ struct CmaState {
     float2 C_half_df[kMaxD * kMaxD];
     float2 m_df[kMaxD];
     float2 sigma_df;
+    KfState kf;
 };
 
 // hi/lo split of a double into a double-float pair (host or device).
@@ -115,6 +140,7 @@ __host__ __device__ inline float2 split_df(double x)
 }
 
 cudaError_t launch_eval(const EvalArgs &a, const LaunchCfg &cfg, cudaStream_t s);
+cudaError_t launch_project_keypoints(const EvalArgs &a, const float *states, int n, float *out, cudaStream_t s);
 size_t tell_smem_bytes();
 cudaError_t launch_eval_batch(const EvalArgs *descs_dev, const uint32_t *const *masks_dev, const int2 *items_dev,
                               int n_items, unsigned *next_item_dev, const LaunchCfg &cfg, int n_clusters,
@@ -147,6 +173,8 @@ struct BatchTables {
 // selected instance (sel[n] device indices, or NULL for instances 0..n-1)
 cudaError_t launch_cma_batch(int op, int n, const int *sel, const BatchTables &t, cudaStream_t s);
 
+static_assert(sizeof(EvalArgs) % 16 == 0, "batched launches copy EvalArgs in 16-byte pieces");
+
 }  // namespace trk
 
 // Objects behind the opaque handles of the C ABI.
@@ -162,7 +190,24 @@ struct trk_tracker {
     uint32_t *zero_mask = nullptr;
     trk::LaunchCfg lc{};
     void *soft = nullptr;       // soft-silhouette scratch, allocated on first use
+    // keypoint term (tracker_set_keypoints / tracker_set_keypoint_obs)
+    int kp_frame[2] = {0, 0};
+    float kp_pt[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    float kp_tau = 0.0f, kp_lambda = 0.0f;
+    const float *kp_obs = nullptr;
 };
+
+// The tracker's keypoint term into a launch's arguments.
+inline void apply_keypoints(trk::EvalArgs &a, const trk_tracker *t)
+{
+    for (int k = 0; k < 2; ++k) {
+        a.kp_frame[k] = t->kp_frame[k];
+        for (int j = 0; j < 3; ++j) a.kp_pt[k][j] = t->kp_pt[k][j];
+    }
+    a.kp_tau = t->kp_tau;
+    a.kp_lambda = t->kp_lambda;
+    a.kp_obs = t->kp_obs;
+}
 
 struct trk_cmaes {
     trk_tracker *t = nullptr;

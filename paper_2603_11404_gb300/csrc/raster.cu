@@ -395,6 +395,79 @@ __device__ __forceinline__ int2 project_vertex(float4 p, const float *Mh, const 
 }
 
 // ----------------------------------------------------------------------------
+// Keypoint term (Eq. kpts_loss): the two keypoints of each instrument (the jaw
+// tips) projected with the candidate's frames, compared with the detections
+// under the better of the two assignments, plus their means, each distance
+// reduced by the threshold tau and clipped at zero; summed over the
+// instruments whose detection is valid (exactly two keypoints found), times
+// lambda_kpts.  FP32 from the double-float frame rows.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ float2 project_keypoint(const float *M, const float *pt, const CamDev &cam)
+{
+    // rows (fx M0, fy M1, M2) as hi/lo pairs: M[r] hi, M[12 + r] lo, r = 4 i + j
+    float X[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        float acc = M[4 * i + 3] + M[12 + 4 * i + 3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) acc = fmaf(M[4 * i + j] + M[12 + 4 * i + j], pt[j], acc);
+        X[i] = acc;
+    }
+    return make_float2(X[0] / X[2] + cam.cx256 * (1.0f / 256.0f), X[1] / X[2] + cam.cy256 * (1.0f / 256.0f));
+}
+
+__device__ __forceinline__ float pos_part(float x) { return fmaxf(x, 0.0f); }
+
+__device__ float keypoint_loss(const EvalArgs &a, const float *sM)
+{
+    const int nF = a.ch.n_frames;
+    float total = 0.0f;
+    for (int b = 0; b < a.ch.n_inst; ++b) {
+        const float *o = a.kp_obs + 5 * b;
+        if (o[4] == 0.0f) continue;
+        const float2 p0 = project_keypoint(sM + (b * nF + a.kp_frame[0]) * 24, a.kp_pt[0], a.cam);
+        const float2 p1 = project_keypoint(sM + (b * nF + a.kp_frame[1]) * 24, a.kp_pt[1], a.cam);
+        const float tau = a.kp_tau;
+        const float same = pos_part(hypotf(o[0] - p0.x, o[1] - p0.y) - tau) + pos_part(hypotf(o[2] - p1.x, o[3] - p1.y) - tau);
+        const float swap = pos_part(hypotf(o[0] - p1.x, o[1] - p1.y) - tau) + pos_part(hypotf(o[2] - p0.x, o[3] - p0.y) - tau);
+        const float mean = pos_part(hypotf(0.5f * (o[0] + o[2]) - 0.5f * (p0.x + p1.x), 0.5f * (o[1] + o[3]) - 0.5f * (p0.y + p1.y)) - tau);
+        total += fminf(same, swap) + mean;
+    }
+    return a.kp_lambda * total;
+}
+
+// Projected keypoints of given states (synthetic detections, diagnostics):
+// one warp per state composes its frames and writes (u, v) of both keypoints
+// of every instrument.
+__global__ void k_project_keypoints(EvalArgs a, const float *states, int n, float *out)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int nI = a.ch.n_inst, nF = a.ch.n_frames;
+    float2 *scr = reinterpret_cast<float2 *>(smem);
+    float *sM = reinterpret_cast<float *>(scr + nI * kComposeScratch);
+    const int st = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (st >= n) return;
+    if (warp < nI)
+        compose_frames_warp(a.ch, a.cam, states + (size_t)st * a.d + 9 * warp, sM + warp * nF * 24,
+                            scr + warp * kComposeScratch, lane);
+    __syncthreads();
+    if (threadIdx.x < 2 * nI) {
+        const int b = threadIdx.x >> 1, k = threadIdx.x & 1;
+        const float2 p = project_keypoint(sM + (b * nF + a.kp_frame[k]) * 24, a.kp_pt[k], a.cam);
+        out[((size_t)st * nI + b) * 4 + 2 * k] = p.x;
+        out[((size_t)st * nI + b) * 4 + 2 * k + 1] = p.y;
+    }
+}
+
+cudaError_t launch_project_keypoints(const EvalArgs &a, const float *states, int n, float *out, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    const size_t smem = (size_t)a.ch.n_inst * (kComposeScratch * sizeof(float2) + a.ch.n_frames * 24 * sizeof(float));
+    k_project_keypoints<<<n, 32 * a.ch.n_inst, smem, s>>>(a, states, n, out);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
 // The fused fitness kernel.
 // ----------------------------------------------------------------------------
 // One candidate c of one evaluation (all CTAs of the cluster call it together).
@@ -619,6 +692,7 @@ __device__ __forceinline__ void eval_candidate(const EvalArgs &a, int c, const u
             } else {
                 L = (float)x;
             }
+            if (a.kp_obs && a.kp_lambda != 0.0f) L = __fadd_rn(L, keypoint_loss(a, sM));
             a.loss[c] = L;
         }
     }

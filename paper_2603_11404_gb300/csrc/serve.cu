@@ -329,6 +329,7 @@ trk_status server_add_stream(trk_server *v, trk_cmaes *es, int32_t generations, 
     a.loss_kind = t->cfg.loss_kind;
     a.lambda_app = t->cfg.lambda_app;
     a.cull = t->cfg.cull_backfaces;
+    apply_keypoints(a, t);
     a.cma_k = es->k;
     a.cma_st = es->st;
     a.cma_y = es->y;

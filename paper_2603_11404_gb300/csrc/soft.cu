@@ -877,6 +877,7 @@ trk_status soft_refine(trk_cmaes *es, const uint32_t *mask_packed_dev, int32_t t
     a.loss_kind = t->cfg.loss_kind;
     a.lambda_app = t->cfg.lambda_app;
     a.cull = t->cfg.cull_backfaces;
+    apply_keypoints(a, t);
     cudaError_t e = launch_eval(a, t->lc, s);
     if (e != cudaSuccess) return soft_fail(TRK_ECUDA, cudaGetErrorString(e));
     k_refine_pick<<<1, 32, 0, s>>>(r->P, r->lh, top_k, d, es->st, pose_out_dev, r->picked);

@@ -377,3 +377,115 @@ def default_scales(d: int) -> np.ndarray:
     for b in range(d // D_PER_INSTRUMENT):
         s[b * 9 + 3: b * 9 + 6] = 2.0
     return s
+
+
+def noisy_detections(tips: np.ndarray, rng: np.random.Generator, sigma_px: float = 2.0,
+                     p_invalid: float = 0.1) -> np.ndarray:
+    """Synthetic keypoint detections from projected true keypoints tips
+    [n_inst, 4] (u1, v1, u2, v2): iid N(0, sigma_px^2) noise per coordinate,
+    the two tips listed in random order, and with probability p_invalid the
+    detection is marked invalid (not exactly two keypoints found).  Returns
+    [n_inst, 5] float32 (x1, y1, x2, y2, valid)."""
+    tips = np.asarray(tips, np.float64)
+    out = np.zeros((tips.shape[0], 5), np.float32)
+    for b in range(tips.shape[0]):
+        t = tips[b].reshape(2, 2) + rng.normal(size=(2, 2)) * sigma_px
+        if rng.random() < 0.5:
+            t = t[::-1]
+        out[b, :4] = t.reshape(-1)
+        out[b, 4] = 0.0 if rng.random() < p_invalid else 1.0
+    return out
+
+
+# --------------------------------------------------------------------------
+# Paper-style synthetic workload (the synthetic set of Sec. IV: 700x493
+# frames, smooth random motion, mask corruption by morphology and blobs)
+# --------------------------------------------------------------------------
+def paper_intrinsics() -> Intrinsics:
+    return Intrinsics(700.0, 700.0, 350.0, 246.5, 700, 493)
+
+
+def lookat_from_matrix(R: np.ndarray) -> np.ndarray:
+    """Angles (alpha, beta, gamma) with R = Ry(gamma) Rx(alpha) Rz(beta)."""
+    alpha = math.atan2(-R[1, 2], math.hypot(R[0, 2], R[2, 2]))
+    gamma = math.atan2(R[0, 2], R[2, 2])
+    beta = math.atan2(R[1, 0], R[1, 1])
+    return np.array([alpha, beta, gamma])
+
+
+def matrix_from_lookat(a: np.ndarray) -> np.ndarray:
+    from scipy.spatial.transform import Rotation
+    return (Rotation.from_euler("y", a[2]) * Rotation.from_euler("x", a[0]) * Rotation.from_euler("z", a[1])).as_matrix()
+
+
+def state_lookat_to_axis_angle(x: np.ndarray) -> np.ndarray:
+    """Same pose with the rotation as an axis-angle vector (per instrument)."""
+    out = np.array(x, np.float64)
+    for b in range(len(out) // D_PER_INSTRUMENT):
+        out[9 * b: 9 * b + 3] = _rotvec_from_matrix(matrix_from_lookat(out[9 * b: 9 * b + 3]))
+    return out
+
+
+def paper_trajectory(rng: np.random.Generator, p0: np.ndarray, n_frames: int, fps: float = 30.0,
+                     seg_s: float = 1.0, amp_mm: float = 10.0, amp_rad: float = 0.3, ou_theta: float = 2.0,
+                     ou_sigma: float = 0.05, smooth: float = 0.3) -> np.ndarray:
+    """[n_frames, d] states: cubic Hermite spline through random waypoints
+    (every seg_s seconds, offsets U[-amp, amp] around p0, Catmull-Rom
+    tangents), plus Ornstein-Uhlenbeck noise (rate ou_theta, scale ou_sigma x
+    amp), low-pass filtered by exponential smoothing (factor smooth); jaw
+    coordinates clamped to [0, 0.8]."""
+    d = p0.shape[0]
+    A = np.full(d, amp_rad)
+    for b in range(d // D_PER_INSTRUMENT):
+        A[b * 9 + 3: b * 9 + 6] = amp_mm
+    n_seg = int(math.ceil(n_frames / (seg_s * fps))) + 3
+    W = p0[None, :] + rng.uniform(-1, 1, size=(n_seg, d)) * A[None, :]
+    T = np.zeros_like(W)
+    T[1:-1] = 0.5 * (W[2:] - W[:-2])
+    out = np.zeros((n_frames, d))
+    ou = np.zeros(d)
+    dt = 1.0 / fps
+    y = None
+    for f in range(n_frames):
+        u = f / (seg_s * fps)
+        k = int(u) + 1
+        t = u - int(u)
+        h00, h10, h01, h11 = 2 * t**3 - 3 * t**2 + 1, t**3 - 2 * t**2 + t, -2 * t**3 + 3 * t**2, t**3 - t**2
+        x = h00 * W[k] + h10 * T[k] + h01 * W[k + 1] + h11 * T[k + 1]
+        ou += -ou_theta * ou * dt + ou_sigma * A * math.sqrt(dt) * rng.normal(size=d)
+        x = x + ou
+        y = x if y is None else smooth * x + (1 - smooth) * y
+        out[f] = y
+    for b in range(d // D_PER_INSTRUMENT):
+        out[:, b * 9 + 8] = np.clip(out[:, b * 9 + 8], 0.0, 0.8)
+    return out
+
+
+def paper_corrupt_mask(mask: np.ndarray, rng: np.random.Generator, max_radius: int = 2, n_blobs: int = 6,
+                       blob_r=(2.0, 8.0), flip_p: float = 0.0) -> np.ndarray:
+    """Observed mask = clean mask dilated or eroded by a random radius
+    (0..max_radius px, square structuring element), then n_blobs disks centred
+    on random boundary pixels, each added or removed with equal odds."""
+    from scipy import ndimage
+    m = mask.astype(bool)
+    r = int(rng.integers(0, max_radius + 1))
+    if r > 0:
+        st = np.ones((2 * r + 1, 2 * r + 1), bool)
+        m = ndimage.binary_dilation(m, st) if rng.random() < 0.5 else ndimage.binary_erosion(m, st)
+    edge = m ^ ndimage.binary_erosion(m)
+    pts = np.argwhere(edge)
+    H, W = m.shape
+    for _ in range(n_blobs if len(pts) else 0):
+        ci, cj = pts[rng.integers(len(pts))]
+        rad = rng.uniform(*blob_r)
+        i0, i1 = max(0, int(ci - rad)), min(H, int(ci + rad) + 1)
+        j0, j1 = max(0, int(cj - rad)), min(W, int(cj + rad) + 1)
+        ii, jj = np.mgrid[i0:i1, j0:j1]
+        disk = (ii - ci) ** 2 + (jj - cj) ** 2 <= rad * rad
+        if rng.random() < 0.5:
+            m[i0:i1, j0:j1] |= disk
+        else:
+            m[i0:i1, j0:j1] &= ~disk
+    if flip_p > 0:
+        m ^= rng.random(m.shape) < flip_p
+    return m.astype(np.uint8)
