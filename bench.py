@@ -72,6 +72,23 @@ def _args():
     return p.parse_args()
 
 
+def max_over_ranks(x: float, ws: int, device) -> float:
+    """The largest value of x over the ranks (the job's time is its slowest rank's)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(ws: int, steps: int, units_per_step: float, max_seconds: float) -> float:
+    """Whole-job throughput: the units every rank processed (replicas: ws x
+    steps x units per step) over the slowest rank's time."""
+    return ws * steps * units_per_step / max_seconds
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -202,13 +219,11 @@ def run_ours(a):
         torch.cuda.synchronize()
     step_ms = np.array([s.elapsed_time(e) for s, e in evs])
     total_s = float(step_ms.sum()) / 1e3
+    total_s = max_over_ranks(total_s, ws, "cuda")
     if ws > 1:
-        t = torch.tensor([total_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
         dist.barrier()
     evals = ws * a.steps * LAM * GENS
-    value = evals / total_s
+    value = job_throughput(ws, a.steps, LAM * GENS, total_s)
     pose_err = np.abs(poses[a.warmup:].cpu().numpy() - traj[a.warmup:].astype(np.float32))
 
     # ---- e2e: the public host call (mask H2D from pinned memory, pose D2H) ----
@@ -223,11 +238,7 @@ def run_ours(a):
         t0 = time.perf_counter()
         es2.track_frame_host(masks_pinned[f], GENS)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_total = sum(e2e_ms) / 1e3
-    if ws > 1:
-        t = torch.tensor([e2e_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = max_over_ranks(sum(e2e_ms) / 1e3, ws, "cuda")
 
     # ---- dominant kernel: the fused fitness launch on this run's populations ----
     R = min(100, a.steps)
