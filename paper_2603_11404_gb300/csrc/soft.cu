@@ -18,8 +18,9 @@
 //                   state tangents carried along (forward mode), vertex
 //                   projection, screen box of the instrument
 //   k_soft_tribox   per (candidate, triangle): window of influence (bounding
-//                   box grown by 14 sigma) clipped to the image
-//   k_soft_tile     per (candidate, 32x32 tile): pass 1 sums the softplus
+//                   box grown by 14 sigma) clipped to the image, and the union
+//                   of the windows of every chunk of 256 triangles
+//   k_soft_tile     per (candidate, 16x16 tile): pass 1 sums the softplus
 //                   terms of every triangle whose window meets the tile into
 //                   the tile's pixels and adds the tile's squared error to the
 //                   loss; with a gradient, pass 2 recomputes the same pairs
@@ -37,7 +38,7 @@
 namespace trk {
 
 constexpr float kSoftCutoff = 14.0f;   // in units of sigma
-constexpr int kTile = 32;              // tile edge (px); one mask word per tile row
+constexpr int kTile = 16;              // tile edge (px): one pixel per thread
 constexpr int kSoftThreads = 256;
 constexpr int kChunk = 256;            // triangles staged per pass
 
@@ -240,6 +241,8 @@ struct SoftArgs {
     float2 *gv;               // [lam * nI * V]: dL/du, dL/dv
     float *dT;                // [lam * nI * nF * 9 * 12]
     short4 *box;              // [lam * nI * T]: window j0, i0, j1, i1 (j0 > j1: none)
+    int4 *cbox;               // [lam * nchunk]: union of the windows of each chunk
+    int nchunk;
     int4 *ibox;               // [lam * nI]: window of the instrument
     double *lacc;             // [lam]
     float *loss;              // [lam]
@@ -303,30 +306,44 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft_project(SoftArgs a)
         a.ibox[(size_t)c * a.nI + b] = make_int4(max(bx[0], 0), max(bx[1], 0), min(bx[2], a.W - 1), min(bx[3], a.H - 1));
 }
 
-// Window of influence of every triangle (none for a flagged vertex or zero area).
-__global__ void __launch_bounds__(256) k_soft_tribox(SoftArgs a)
+// Window of influence of every triangle (none for a flagged vertex or zero
+// area), and the union of the windows of each chunk of kChunk triangles (one
+// block per chunk), so that a tile skips whole chunks that cannot reach it.
+__global__ void __launch_bounds__(kChunk) k_soft_tribox(SoftArgs a)
 {
     const int c = blockIdx.y;
     const int NT = a.nI * a.T;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= NT) return;
-    const int b = t >= a.T;
-    const int4 tri = a.tris[t - b * a.T];
-    const float4 *sv = a.sv + ((size_t)c * a.nI + b) * a.V;
-    const float4 p0 = sv[tri.x], p1 = sv[tri.y], p2 = sv[tri.z];
+    const int t = blockIdx.x * kChunk + threadIdx.x;
+    __shared__ int cb[4];
+    if (threadIdx.x < 4) cb[threadIdx.x] = (threadIdx.x < 2) ? INT_MAX : INT_MIN;
+    __syncthreads();
     short4 o = make_short4(1, 1, 0, 0);
-    if (p0.w == 0.0f && p1.w == 0.0f && p2.w == 0.0f) {
-        const float A = (p1.x - p0.x) * (p2.y - p0.y) - (p1.y - p0.y) * (p2.x - p0.x);
-        if (A != 0.0f) {
-            const float m = kSoftCutoff * a.sigma;
-            const int j0 = max(0, (int)ceilf(fminf(p0.x, fminf(p1.x, p2.x)) + a.cx - m));
-            const int j1 = min(a.W - 1, (int)floorf(fmaxf(p0.x, fmaxf(p1.x, p2.x)) + a.cx + m));
-            const int i0 = max(0, (int)ceilf(fminf(p0.y, fminf(p1.y, p2.y)) + a.cy - m));
-            const int i1 = min(a.H - 1, (int)floorf(fmaxf(p0.y, fmaxf(p1.y, p2.y)) + a.cy + m));
-            if (j0 <= j1 && i0 <= i1) o = make_short4((short)j0, (short)i0, (short)j1, (short)i1);
+    if (t < NT) {
+        const int b = t >= a.T;
+        const int4 tri = a.tris[t - b * a.T];
+        const float4 *sv = a.sv + ((size_t)c * a.nI + b) * a.V;
+        const float4 p0 = sv[tri.x], p1 = sv[tri.y], p2 = sv[tri.z];
+        if (p0.w == 0.0f && p1.w == 0.0f && p2.w == 0.0f) {
+            const float A = (p1.x - p0.x) * (p2.y - p0.y) - (p1.y - p0.y) * (p2.x - p0.x);
+            if (A != 0.0f) {
+                const float m = kSoftCutoff * a.sigma;
+                const int j0 = max(0, (int)ceilf(fminf(p0.x, fminf(p1.x, p2.x)) + a.cx - m));
+                const int j1 = min(a.W - 1, (int)floorf(fmaxf(p0.x, fmaxf(p1.x, p2.x)) + a.cx + m));
+                const int i0 = max(0, (int)ceilf(fminf(p0.y, fminf(p1.y, p2.y)) + a.cy - m));
+                const int i1 = min(a.H - 1, (int)floorf(fmaxf(p0.y, fmaxf(p1.y, p2.y)) + a.cy + m));
+                if (j0 <= j1 && i0 <= i1) {
+                    o = make_short4((short)j0, (short)i0, (short)j1, (short)i1);
+                    atomicMin(&cb[0], j0);
+                    atomicMin(&cb[1], i0);
+                    atomicMax(&cb[2], j1);
+                    atomicMax(&cb[3], i1);
+                }
+            }
         }
+        a.box[(size_t)c * NT + t] = o;
     }
-    a.box[(size_t)c * NT + t] = o;
+    __syncthreads();
+    if (threadIdx.x == 0) a.cbox[(size_t)c * a.nchunk + blockIdx.x] = make_int4(cb[0], cb[1], cb[2], cb[3]);
 }
 
 // Staged triangle: positively oriented image-space vertices, edge data, window.
@@ -443,6 +460,13 @@ __device__ void stage_chunk(const SoftArgs &a, int c, int t0, int tx0, int ty0, 
     __syncthreads();
 }
 
+// Does chunk k of candidate c have a window reaching the tile?
+__device__ __forceinline__ bool chunk_reaches(const SoftArgs &a, int c, int k, int tx0, int ty0)
+{
+    const int4 b = a.cbox[(size_t)c * a.nchunk + k];
+    return b.x <= b.z && b.x <= tx0 + kTile - 1 && b.z >= tx0 && b.y <= ty0 + kTile - 1 && b.w >= ty0;
+}
+
 __global__ void __launch_bounds__(kSoftThreads) k_soft_tile(SoftArgs a)
 {
     const int c = blockIdx.y;
@@ -452,96 +476,89 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft_tile(SoftArgs a)
     __shared__ SoftTriSmem S;
     __shared__ float wpx[kTile * kTile];
     __shared__ float red[8];
-    // pixels of this thread: column tx0 + lane, rows ty0 + warp + 8 r
-    const int j = tx0 + lane;
-    const float px = (float)j, inv_s = 1.0f / a.sigma, cut = -kSoftCutoff * a.sigma;
-    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    // this thread's pixel in the forward pass
+    const int j = tx0 + (tid & (kTile - 1)), i = ty0 + tid / kTile;
+    const float px = (float)j, py = (float)i, inv_s = 1.0f / a.sigma, cut = -kSoftCutoff * a.sigma;
+    float acc = 0.0f;
     // is the tile within reach of any instrument?
     bool near = false;
     for (int b = 0; b < a.nI; ++b) {
         const int4 ib = a.ibox[(size_t)c * a.nI + b];
         near |= ib.x <= ib.z && ib.x <= tx0 + kTile - 1 && ib.z >= tx0 && ib.y <= ty0 + kTile - 1 && ib.w >= ty0;
     }
-    const int NT = a.nI * a.T;
     if (near) {
-        for (int t0 = 0; t0 < NT; t0 += kChunk) {
-            stage_chunk(a, c, t0, tx0, ty0, S);
+        for (int k = 0; k < a.nchunk; ++k) {
+            if (!chunk_reaches(a, c, k, tx0, ty0)) continue;  // the same decision in every thread
+            stage_chunk(a, c, k * kChunk, tx0, ty0, S);
             const int n = S.n;
             for (int e = 0; e < n; ++e) {
                 const short4 w = S.win[e];
-                if (j < w.x || j > w.z) continue;
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const int i = ty0 + warp + 8 * r;
-                    if (i < w.y || i > w.w) continue;
-                    int kind, kf;
-                    const float d = soft_distance(S, e, px, (float)i, kind, kf);
-                    if (d >= cut) acc[r] += softplusf(d * inv_s);
-                }
+                if (j < w.x || j > w.z || i < w.y || i > w.w) continue;
+                int kind, kf;
+                const float d = soft_distance(S, e, px, py, kind, kf);
+                if (d >= cut) acc += softplusf(d * inv_s);
             }
             __syncthreads();
         }
     }
     // squared error of the tile's pixels; per-pixel factor of the backward
-    float l = 0.0f;
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int i = ty0 + warp + 8 * r;
-        float wp = 0.0f;
-        if (i < a.H && j < a.W) {
-            const float Sv = 1.0f - __expf(-acc[r]);
-            const float Mv = (float)((a.mask[(size_t)i * a.Wq + (tx0 >> 5)] >> lane) & 1u);
-            const float e = Sv - Mv;
-            l = fmaf(e, e, l);
-            wp = 2.0f * e * (1.0f - Sv) * inv_s;
-        }
-        wpx[(warp + 8 * r) * kTile + lane] = wp;
+    float l = 0.0f, wp = 0.0f;
+    if (i < a.H && j < a.W) {
+        const float Sv = 1.0f - __expf(-acc);
+        const float Mv = (float)((a.mask[(size_t)i * a.Wq + (j >> 5)] >> (j & 31)) & 1u);
+        const float e = Sv - Mv;
+        l = e * e;
+        wp = 2.0f * e * (1.0f - Sv) * inv_s;
     }
+    wpx[tid] = wp;
     for (int o = 16; o; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
     if (lane == 0) red[warp] = l;
     __syncthreads();
     if (tid == 0) {
-        double s = 0.0;
-        for (int w = 0; w < 8; ++w) s += (double)red[w];
-        atomicAdd(&a.lacc[c], s);
+        double sum = 0.0;
+        for (int w = 0; w < 8; ++w) sum += (double)red[w];
+        atomicAdd(&a.lacc[c], sum);
     }
     if (!a.grad || !near) return;
-    // pass 2: the same pairs again, one warp per staged triangle
-    for (int t0 = 0; t0 < NT; t0 += kChunk) {
-        stage_chunk(a, c, t0, tx0, ty0, S);
+    // pass 2: the same pairs again, one warp per staged triangle, lanes over
+    // two rows of 16 pixels at a time
+    const int cj = tx0 + (lane & (kTile - 1)), rsub = lane / kTile;
+    const float cpx = (float)cj;
+    for (int k = 0; k < a.nchunk; ++k) {
+        if (!chunk_reaches(a, c, k, tx0, ty0)) continue;
+        stage_chunk(a, c, k * kChunk, tx0, ty0, S);
         const int n = S.n;
         for (int e = warp; e < n; e += 8) {
             const short4 w = S.win[e];
             float g[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+            const bool colin = cj >= w.x && cj <= w.z && cj < a.W;
             const int ia = max((int)w.y, ty0), ib = min((int)w.w, min(ty0 + kTile - 1, a.H - 1));
-            const bool colin = j >= w.x && j <= w.z && j < a.W;
-            for (int i = ia; i <= ib; ++i) {
-                if (!colin) continue;
+            for (int i2 = ia + rsub; i2 <= ib; i2 += 2) {
+                if (!colin) break;
                 int kind, kf;
-                const float py = (float)i;
-                const float d = soft_distance(S, e, px, py, kind, kf);
+                const float cpy = (float)i2;
+                const float d = soft_distance(S, e, cpx, cpy, kind, kf);
                 if (d < cut) continue;
-                const float gd = wpx[(i - ty0) * kTile + lane] * sigmoidf_(d * inv_s);
+                const float gd = wpx[(i2 - ty0) * kTile + (cj - tx0)] * sigmoidf_(d * inv_s);
                 const int k1 = kf == 2 ? 0 : kf + 1;
                 const float x0 = S.x[kf][e], y0 = S.y[kf][e], dx = S.ex[kf][e], dy = S.ey[kf][e];
                 if (kind == 0) {
                     // d = E / L (inside, or outside at the segment interior: d = -|E|/L = E/L there)
-                    const float E = fmaf(dx, py - y0, -dy * (px - x0));
+                    const float E = fmaf(dx, cpy - y0, -dy * (cpx - x0));
                     const float il = S.il[kf][e], il2 = S.il2[kf][e];
                     const float h = E * il;
-                    float s = 1.0f;
-                    if (d < 0.0f && E > 0.0f) s = -1.0f;  // outside on the inner side of the line
+                    float sg = 1.0f;
+                    if (d < 0.0f && E > 0.0f) sg = -1.0f;  // outside on the inner side of the line
                     const float x1 = x0 + dx, y1 = y0 + dy;
                     // d(E/L) = dE / L - (E / L^2) dL, dL = (-dx, -dy, dx, dy) / L
-                    g[2 * kf] += gd * s * ((y1 - py) * il + h * dx * il2);
-                    g[2 * kf + 1] += gd * s * ((px - x1) * il + h * dy * il2);
-                    g[2 * k1] += gd * s * ((py - y0) * il - h * dx * il2);
-                    g[2 * k1 + 1] += gd * s * (-(px - x0) * il - h * dy * il2);
+                    g[2 * kf] += gd * sg * ((y1 - cpy) * il + h * dx * il2);
+                    g[2 * kf + 1] += gd * sg * ((cpx - x1) * il + h * dy * il2);
+                    g[2 * k1] += gd * sg * ((cpy - y0) * il - h * dx * il2);
+                    g[2 * k1 + 1] += gd * sg * (-(cpx - x0) * il - h * dy * il2);
                 } else {
                     // d = -|p - v|: dd/dv = (p - v) / |p - v|
                     const int kv = kind == 1 ? kf : k1;
-                    const float vx = S.x[kv][e], vy = S.y[kv][e];
-                    const float rx = px - vx, ry = py - vy;
+                    const float rx = cpx - S.x[kv][e], ry = cpy - S.y[kv][e];
                     const float rl = rsqrtf(fmaxf(fmaf(rx, rx, ry * ry), 1e-30f));
                     g[2 * kv] += gd * rx * rl;
                     g[2 * kv + 1] += gd * ry * rl;
@@ -684,6 +701,7 @@ struct SoftScratch {
     float *dT = nullptr;
     short4 *box = nullptr;
     int4 *ibox = nullptr;
+    int4 *cbox = nullptr;
     double *lacc = nullptr;
 };
 
@@ -716,6 +734,7 @@ trk_status soft_scratch(trk_tracker *t, int lam, SoftScratch **out)
         (e = cudaMalloc(&s->dT, sizeof(float) * (size_t)lam * nI * t->ch.n_frames * 9 * 12)) != cudaSuccess ||
         (e = cudaMalloc(&s->box, sizeof(short4) * (size_t)lam * nI * t->T)) != cudaSuccess ||
         (e = cudaMalloc(&s->ibox, sizeof(int4) * (size_t)lam * nI)) != cudaSuccess ||
+        (e = cudaMalloc(&s->cbox, sizeof(int4) * (size_t)lam * ((nI * t->T + kChunk - 1) / kChunk))) != cudaSuccess ||
         (e = cudaMalloc(&s->lacc, sizeof(double) * lam)) != cudaSuccess) {
         t->soft = s;
         soft_free(t);
@@ -764,11 +783,12 @@ trk_status soft_launch(trk_tracker *t, const float *params, int lam, const uint3
     a.box = s->box;
     a.ibox = s->ibox;
     a.lacc = s->lacc;
+    a.cbox = s->cbox;
+    a.nchunk = (a.nI * a.T + kChunk - 1) / kChunk;
     a.loss = loss;
     a.grad = grad;
-    const int NT = a.nI * a.T;
     k_soft_project<<<dim3(lam, a.nI), kSoftThreads, 0, st>>>(a);
-    k_soft_tribox<<<dim3((NT + 255) / 256, lam), 256, 0, st>>>(a);
+    k_soft_tribox<<<dim3(a.nchunk, lam), kChunk, 0, st>>>(a);
     k_soft_tile<<<dim3(a.ntx * a.nty, lam), kSoftThreads, 0, st>>>(a);
     k_soft_reduce<<<dim3(lam, a.nI), kSoftThreads, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
@@ -786,6 +806,7 @@ void trk::soft_free(trk_tracker *t)
     cudaFree(s->dT);
     cudaFree(s->box);
     cudaFree(s->ibox);
+    cudaFree(s->cbox);
     cudaFree(s->lacc);
     delete s;
     t->soft = nullptr;
