@@ -158,6 +158,160 @@ __device__ __forceinline__ void sandwich64(int d, const double *X, const double 
     __syncthreads();
 }
 
+// One-sided Jacobi, columns in shared memory (any d): Xc, Jc column-major
+// d x d; called by one warp.
+template <int D>  // D > 0: the dimension as a compile-time constant (cheap index arithmetic)
+static __device__ __noinline__ void onesided_jacobi_smem(float *Xc, float *Jc, int dyn_d, int lane, CmaState *st)
+{
+    const int d = D > 0 ? D : dyn_d, n2 = d + (d & 1);
+    float amax = 0.0f;  // largest squared column norm, for the absolute floor
+    if (lane < d)
+        for (int q = 0; q < d; ++q) amax = fmaxf(amax, Xc[lane * d + q] * Xc[lane * d + q]);
+    for (int o = 16; o; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    int sweeps = 0;
+    for (; sweeps < 12; ++sweeps) {
+        bool rotated = false;
+        float rho = 0.0f;  // largest |u . w| / (|u| |w|) rotated in this sweep
+        for (int r = 0; r < n2 - 1; ++r) {
+            // circle method: position n2-1 meets r, the others pair as (r+i, r-i) mod n2-1
+            int partner;
+            if (lane == n2 - 1) partner = r;
+            else if (lane == r) partner = n2 - 1;
+            else partner = (2 * r - lane + 2 * (n2 - 1)) % (n2 - 1);
+            const bool act = lane < d && partner < d;
+            const int lo = min(lane, partner), hi = max(lane, partner);
+            float c = 1.0f, sn = 0.0f;
+            float xo[kMaxD], vo[kMaxD];
+            if (act) {
+                float a = 0.0f, b = 0.0f, g = 0.0f;
+#pragma unroll
+                for (int q = 0; q < kMaxD; ++q)
+                    if (q < d) {
+                        const float u = Xc[lo * d + q], w = Xc[hi * d + q];
+                        a = fmaf(u, u, a);
+                        b = fmaf(w, w, b);
+                        g = fmaf(u, w, g);
+                    }
+                if (g * g > 1e-10f * a * b + 1e-22f * amax * amax) {
+                    const float zeta = (b - a) / (2.0f * g);
+                    const float t = copysignf(1.0f, zeta) / (fabsf(zeta) + sqrtf(1.0f + zeta * zeta));
+                    c = rsqrtf(1.0f + t * t);
+                    sn = t * c;
+                    rotated = true;
+                    rho = fmaxf(rho, fabsf(g) * rsqrtf(a * b));
+                }
+                // own column after the rotation: lo gets c u - s w, hi gets s u + c w
+                const bool is_lo = lane == lo;
+#pragma unroll
+                for (int q = 0; q < kMaxD; ++q)
+                    if (q < d) {
+                        const float u = Xc[lo * d + q], w = Xc[hi * d + q];
+                        const float ju = Jc[lo * d + q], jw = Jc[hi * d + q];
+                        xo[q] = is_lo ? fmaf(c, u, -sn * w) : fmaf(sn, u, c * w);
+                        vo[q] = is_lo ? fmaf(c, ju, -sn * jw) : fmaf(sn, ju, c * jw);
+                    }
+            }
+            __syncwarp();
+            if (act) {
+#pragma unroll
+                for (int q = 0; q < kMaxD; ++q)
+                    if (q < d) {
+                        Xc[lane * d + q] = xo[q];
+                        Jc[lane * d + q] = vo[q];
+                    }
+            }
+            __syncwarp();
+        }
+        // Jacobi converges quadratically: after a sweep whose rotations were
+        // all below 1e-3 the columns are orthogonal to ~1e-6 without checking
+        for (int o = 16; o; o >>= 1) rho = fmaxf(rho, __shfl_xor_sync(0xffffffffu, rho, o));
+        if (!__any_sync(0xffffffffu, rotated) || rho < 1e-3f) {
+            ++sweeps;
+            break;
+        }
+    }
+    if (lane == 0) st->jacobi_sweeps = sweeps;
+    }
+
+// The same with the columns in registers (small compile-time D): lane j holds
+// column j of X and of J, and a round exchanges columns by warp shuffles.
+template <int D>
+__device__ __forceinline__ void onesided_jacobi_regs(float *Xc, float *Jc, int lane, CmaState *st)
+{
+    constexpr int N2 = D + (D & 1);
+    float x[D], v[D];
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+        x[q] = lane < D ? Xc[lane * D + q] : 0.0f;
+        v[q] = lane < D ? Jc[lane * D + q] : 0.0f;
+    }
+    float amax = 0.0f;
+#pragma unroll
+    for (int q = 0; q < D; ++q) amax = fmaxf(amax, x[q] * x[q]);
+    for (int o = 16; o; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    const float floor2 = 1e-22f * amax * amax;
+    int sweeps = 0;
+    for (; sweeps < 12; ++sweeps) {
+        bool rotated = false;
+        float rho = 0.0f;
+#pragma unroll 1
+        for (int r = 0; r < N2 - 1; ++r) {
+            int partner = lane;
+            if (lane < N2) {
+                if (lane == N2 - 1) partner = r;
+                else if (lane == r) partner = N2 - 1;
+                else partner = (2 * r - lane + 2 * (N2 - 1)) % (N2 - 1);
+            }
+            const bool act = lane < D && partner < D;
+            const int src = act ? partner : lane;
+            float px[D], pv[D];
+#pragma unroll
+            for (int q = 0; q < D; ++q) {
+                px[q] = __shfl_sync(0xffffffffu, x[q], src);
+                pv[q] = __shfl_sync(0xffffffffu, v[q], src);
+            }
+            if (act) {
+                const bool is_lo = lane < partner;
+                float a = 0.0f, b = 0.0f, g = 0.0f;  // |u|^2, |w|^2, u . w with u = lo, w = hi
+#pragma unroll
+                for (int q = 0; q < D; ++q) {
+                    const float u = is_lo ? x[q] : px[q], w = is_lo ? px[q] : x[q];
+                    a = fmaf(u, u, a);
+                    b = fmaf(w, w, b);
+                    g = fmaf(u, w, g);
+                }
+                if (g * g > 1e-10f * a * b + floor2) {
+                    const float zeta = (b - a) / (2.0f * g);
+                    const float t = copysignf(1.0f, zeta) / (fabsf(zeta) + sqrtf(1.0f + zeta * zeta));
+                    const float c = rsqrtf(1.0f + t * t), sn = t * c;
+                    rotated = true;
+                    rho = fmaxf(rho, fabsf(g) * rsqrtf(a * b));
+#pragma unroll
+                    for (int q = 0; q < D; ++q) {
+                        const float u = is_lo ? x[q] : px[q], w = is_lo ? px[q] : x[q];
+                        const float ju = is_lo ? v[q] : pv[q], jw = is_lo ? pv[q] : v[q];
+                        x[q] = is_lo ? fmaf(c, u, -sn * w) : fmaf(sn, u, c * w);
+                        v[q] = is_lo ? fmaf(c, ju, -sn * jw) : fmaf(sn, ju, c * jw);
+                    }
+                }
+            }
+        }
+        for (int o = 16; o; o >>= 1) rho = fmaxf(rho, __shfl_xor_sync(0xffffffffu, rho, o));
+        if (!__any_sync(0xffffffffu, rotated) || rho < 1e-3f) {
+            ++sweeps;
+            break;
+        }
+    }
+    if (lane < D)
+#pragma unroll
+        for (int q = 0; q < D; ++q) {
+            Xc[lane * D + q] = x[q];
+            Jc[lane * D + q] = v[q];
+        }
+    if (lane == 0) st->jacobi_sweeps = sweeps;
+    __syncwarp();
+}
+
 // The whole update from the fitness of the last population (called by every
 // thread of one block).  y [lam*d] are the FP64 steps of that population.
 // DC is the dimension as a compile-time constant (0 = read k.d at run time):
@@ -311,75 +465,10 @@ __device__ __forceinline__ void cma_tell_impl(const CmaConst &k, CmaState *st, c
     }
     __syncthreads();
     if (tid < 32) {
-        const int lane = tid, n2 = d + (d & 1);
-        float *Xc = S.Af, *Jc = S.Vf2;
-        float amax = 0.0f;  // largest squared column norm, for the absolute floor
-        if (lane < d)
-            for (int q = 0; q < d; ++q) amax = fmaxf(amax, Xc[lane * d + q] * Xc[lane * d + q]);
-        for (int o = 16; o; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-        int sweeps = 0;
-        for (; sweeps < 12; ++sweeps) {
-            bool rotated = false;
-            float rho = 0.0f;  // largest |u . w| / (|u| |w|) rotated in this sweep
-            for (int r = 0; r < n2 - 1; ++r) {
-                // circle method: position n2-1 meets r, the others pair as (r+i, r-i) mod n2-1
-                int partner;
-                if (lane == n2 - 1) partner = r;
-                else if (lane == r) partner = n2 - 1;
-                else partner = (2 * r - lane + 2 * (n2 - 1)) % (n2 - 1);
-                const bool act = lane < d && partner < d;
-                const int lo = min(lane, partner), hi = max(lane, partner);
-                float c = 1.0f, sn = 0.0f;
-                float xo[kMaxD], vo[kMaxD];
-                if (act) {
-                    float a = 0.0f, b = 0.0f, g = 0.0f;
-#pragma unroll
-                    for (int q = 0; q < kMaxD; ++q)
-                        if (q < d) {
-                            const float u = Xc[lo * d + q], w = Xc[hi * d + q];
-                            a = fmaf(u, u, a);
-                            b = fmaf(w, w, b);
-                            g = fmaf(u, w, g);
-                        }
-                    if (g * g > 1e-10f * a * b + 1e-22f * amax * amax) {
-                        const float zeta = (b - a) / (2.0f * g);
-                        const float t = copysignf(1.0f, zeta) / (fabsf(zeta) + sqrtf(1.0f + zeta * zeta));
-                        c = rsqrtf(1.0f + t * t);
-                        sn = t * c;
-                        rotated = true;
-                        rho = fmaxf(rho, fabsf(g) * rsqrtf(a * b));
-                    }
-                    // own column after the rotation: lo gets c u - s w, hi gets s u + c w
-                    const bool is_lo = lane == lo;
-#pragma unroll
-                    for (int q = 0; q < kMaxD; ++q)
-                        if (q < d) {
-                            const float u = Xc[lo * d + q], w = Xc[hi * d + q];
-                            const float ju = Jc[lo * d + q], jw = Jc[hi * d + q];
-                            xo[q] = is_lo ? fmaf(c, u, -sn * w) : fmaf(sn, u, c * w);
-                            vo[q] = is_lo ? fmaf(c, ju, -sn * jw) : fmaf(sn, ju, c * jw);
-                        }
-                }
-                __syncwarp();
-                if (act) {
-#pragma unroll
-                    for (int q = 0; q < kMaxD; ++q)
-                        if (q < d) {
-                            Xc[lane * d + q] = xo[q];
-                            Jc[lane * d + q] = vo[q];
-                        }
-                }
-                __syncwarp();
-            }
-            // Jacobi converges quadratically: after a sweep whose rotations were
-            // all below 1e-3 the columns are orthogonal to ~1e-6 without checking
-            for (int o = 16; o; o >>= 1) rho = fmaxf(rho, __shfl_xor_sync(0xffffffffu, rho, o));
-            if (!__any_sync(0xffffffffu, rotated) || rho < 1e-3f) {
-                ++sweeps;
-                break;
-            }
-        }
-        if (lane == 0) st->jacobi_sweeps = sweeps;
+        if constexpr (DC > 0 && DC <= 12)
+            onesided_jacobi_regs<DC>(S.Af, S.Vf2, tid, st);
+        else
+            onesided_jacobi_smem<DC>(S.Af, S.Vf2, d, tid, st);
     }
     if (tid == (nt > 32 ? 32 : 0)) {
         // step size (CSA): on the second warp, off the eigendecomposition's critical path
