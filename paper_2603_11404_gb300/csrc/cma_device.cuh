@@ -193,8 +193,10 @@ static __device__ __noinline__ void onesided_jacobi_smem(float *Xc, float *Jc, i
                         g = fmaf(u, w, g);
                     }
                 if (g * g > 1e-10f * a * b + 1e-22f * amax * amax) {
-                    const float zeta = (b - a) / (2.0f * g);
-                    const float t = copysignf(1.0f, zeta) / (fabsf(zeta) + sqrtf(1.0f + zeta * zeta));
+                    // approximate intrinsics are enough: any rotation close to the
+                    // annihilating one converges, and the test above uses exact g, a, b
+                    const float zeta = __fdividef(b - a, 2.0f * g), h = fmaf(zeta, zeta, 1.0f);
+                    const float t = copysignf(__fdividef(1.0f, fabsf(zeta) + h * rsqrtf(h)), zeta);
                     c = rsqrtf(1.0f + t * t);
                     sn = t * c;
                     rotated = true;
@@ -281,8 +283,10 @@ __device__ __forceinline__ void onesided_jacobi_regs(float *Xc, float *Jc, int l
                     g = fmaf(u, w, g);
                 }
                 if (g * g > 1e-10f * a * b + floor2) {
-                    const float zeta = (b - a) / (2.0f * g);
-                    const float t = copysignf(1.0f, zeta) / (fabsf(zeta) + sqrtf(1.0f + zeta * zeta));
+                    // approximate intrinsics are enough: any rotation close to the
+                    // annihilating one converges, and the test above uses exact g, a, b
+                    const float zeta = __fdividef(b - a, 2.0f * g), h = fmaf(zeta, zeta, 1.0f);
+                    const float t = copysignf(__fdividef(1.0f, fabsf(zeta) + h * rsqrtf(h)), zeta);
                     const float c = rsqrtf(1.0f + t * t), sn = t * c;
                     rotated = true;
                     rho = fmaxf(rho, fabsf(g) * rsqrtf(a * b));
