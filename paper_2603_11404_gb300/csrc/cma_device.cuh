@@ -225,9 +225,9 @@ static __device__ __noinline__ void onesided_jacobi_smem(float *Xc, float *Jc, i
             __syncwarp();
         }
         // Jacobi converges quadratically: after a sweep whose rotations were
-        // all below 1e-3 the columns are orthogonal to ~1e-6 without checking
+        // all below 3e-3 the columns are orthogonal to ~1e-5 without checking
         for (int o = 16; o; o >>= 1) rho = fmaxf(rho, __shfl_xor_sync(0xffffffffu, rho, o));
-        if (!__any_sync(0xffffffffu, rotated) || rho < 1e-3f) {
+        if (!__any_sync(0xffffffffu, rotated) || rho < 3e-3f) {
             ++sweeps;
             break;
         }
@@ -301,7 +301,7 @@ __device__ __forceinline__ void onesided_jacobi_regs(float *Xc, float *Jc, int l
             }
         }
         for (int o = 16; o; o >>= 1) rho = fmaxf(rho, __shfl_xor_sync(0xffffffffu, rho, o));
-        if (!__any_sync(0xffffffffu, rotated) || rho < 1e-3f) {
+        if (!__any_sync(0xffffffffu, rotated) || rho < 3e-3f) {
             ++sweeps;
             break;
         }
