@@ -79,3 +79,32 @@ def test_batch_track_frame_matches_single(api, use_graph):
     for ob, os_ in zip(opt_b, opt_s):
         sa, sb = ob.state(), os_.state()
         assert np.array_equal(sa["C"], sb["C"]) and sa["sigma"] == sb["sigma"]
+
+
+def test_batch_at_the_batching_workload_sizes(api):
+    """Instances at the batching workload's extremes (1280x1024 with a 40k-triangle
+    mesh, a bi-manual 640x512 scene, a 320x256 5k-triangle scene with lambda = 256)
+    in one persistent launch: counts bit-identical to the per-instance launches,
+    and sampled candidates of the largest instance equal to the oracle's."""
+    specs = [("40000", 1, 32, (1280, 1024)), ("20000", 2, 64, (640, 512)), ("5000", 1, 256, (320, 256))]
+    inst = []
+    for k, (mesh, ni, lam, (W, H)) in enumerate(specs):
+        K = wl.Intrinsics(1.25 * W, 1.25 * W, W / 2, H / 2, W, H)
+        sc = wl.make_scene(mesh, "c2", n_instruments=ni, K=K)
+        rng = np.random.default_rng(800 + k)
+        gt = np.concatenate([wl.sample_state(rng, sc.K) for _ in range(ni)])
+        M = wl.corrupt_mask(oracle.render(sc, gt), rng)
+        tr = api.Tracker(sc, loss_kind=wl.LOSS_ONE_MINUS_IOU, lambda_max=lam)
+        P = wl.population_around(rng, gt, lam)
+        inst.append(dict(sc=sc, tr=tr, M=M, Mp=tr.pack_mask(torch.from_numpy(M).cuda()), P=P,
+                         Pd=torch.from_numpy(P).cuda()))
+    b = api.Batch([x["tr"] for x in inst], lams=[x["P"].shape[0] for x in inst])
+    losses, counts = b.eval([x["Pd"] for x in inst], [x["Mp"] for x in inst])
+    torch.cuda.synchronize()
+    for x, l, c in zip(inst, losses, counts):
+        rl, rc = x["tr"].eval_population(x["Pd"], x["Mp"], counts=True)
+        assert torch.equal(c, rc) and torch.equal(l.view(torch.int32), rl.view(torch.int32))
+    big = inst[0]
+    ref = oracle.eval_population(big["sc"], big["P"][[0, 31]], big["M"], n_threads=4)
+    c = counts[0].cpu().numpy()[[0, 31]]
+    assert np.array_equal(c[:, 0], ref["s"]) and np.array_equal(c[:, 1], ref["I"]) and np.array_equal(c[:, 2], ref["m"])
