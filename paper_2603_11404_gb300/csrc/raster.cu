@@ -714,7 +714,20 @@ __device__ __forceinline__ void eval_candidate(const EvalArgs &a, int c, const u
     }
 }
 
-__global__ void __launch_bounds__(256, 4) k_eval(EvalArgs a) { eval_candidate(a, blockIdx.y, nullptr, true); }
+// Programmatic dependent launch: consecutive fused generations are launched
+// with programmatic stream serialisation, so the next generation's CTAs may be
+// scheduled while this one is still running (its last CTA runs the update);
+// they wait for this grid to complete, memory included, before reading
+// anything.  Without that launch attribute both instructions do nothing.
+__device__ __forceinline__ void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;"); }
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+__global__ void __launch_bounds__(256, 4) k_eval(EvalArgs a)
+{
+    griddep_launch_dependents();
+    griddep_wait();
+    eval_candidate(a, blockIdx.y, nullptr, true);
+}
 
 // Persistent batched evaluation: a fixed grid of clusters pulls (instance,
 // candidate) items from a queue (largest first) until it is empty.  CTA 0 of
@@ -813,13 +826,17 @@ cudaError_t launch_eval(const EvalArgs &a, const LaunchCfg &cfg, cudaStream_t s)
     lc.blockDim = dim3(cfg.threads, 1, 1);
     lc.dynamicSmemBytes = cfg.smem;
     lc.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = cfg.cluster;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    // fused generations follow each other: overlap the next one's launch with
+    // this one's tail (see griddep_wait)
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = a.cma_st ? 1 : 0;
     lc.attrs = attr;
-    lc.numAttrs = 1;
+    lc.numAttrs = 2;
     return cudaLaunchKernelEx(&lc, k_eval, a);
 }
 
