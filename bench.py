@@ -68,7 +68,8 @@ def _args():
     p.add_argument("--serve-frames", type=int, default=300, help="frames per camera stream in the serving run")
     p.add_argument("--profile-target", action="store_true",
                    help="run a short fixed launch sequence for ncu (2 warm-up + 3 plain k_eval launches at "
-                        "640x512, lambda = 64, then 3 fused generations) and exit")
+                        "640x512, lambda = 64, then 3 fused generations, then 4 ask / fitness / update rounds) "
+                        "and exit")
     return p.parse_args()
 
 
@@ -744,6 +745,8 @@ def run_profile_target():
     es = api.CMAES(tr, LAM, traj[0], wl.default_scales(9), sigma0=1.0, seed=SEED)
     for _ in range(3):
         es.step(Mp)
+    for _ in range(4):  # the stand-alone update kernel (k_cma_tell), launches 0..3
+        es.tell(tr.eval_population(es.ask(), Mp))
     torch.cuda.synchronize()
     print(json.dumps({"profile_target": "k_eval 640x512 lambda=64", "kernel_digest": _kernel_digest()}))
 
