@@ -276,6 +276,9 @@ class CMAES:
             assert not mask_u8.is_cuda and mask_u8.dtype == torch.uint8 and mask_u8.is_contiguous()
         else:
             mask_u8 = np.ascontiguousarray(mask_u8, np.uint8)
+        K = self.tracker.scene.K
+        if tuple(mask_u8.shape) != (K.height, K.width):
+            raise ValueError(f"mask must be [{K.height}, {K.width}] uint8")
         pose = np.zeros(self.d, np.float32)
         bl = C.c_float()
         jr = None if joint_reading is None else np.ascontiguousarray(joint_reading, np.float32)
@@ -433,7 +436,12 @@ class Server:
     def submit(self, sid: int, mask_u8: np.ndarray, joint_reading=None, tag: int = 0, t_submit: float = -1.0):
         """Queue a frame; returns False (nothing queued) when the staging pool is full."""
         m = np.ascontiguousarray(mask_u8, np.uint8)
+        K = self.optimisers[sid].tracker.scene.K
+        if m.shape != (K.height, K.width):
+            raise ValueError(f"mask must be [{K.height}, {K.width}] uint8")
         j = None if joint_reading is None else np.ascontiguousarray(joint_reading, np.float32)
+        if j is not None and j.size != 3 * self.optimisers[sid].tracker.scene.n_instruments:
+            raise ValueError("joint readings must have 3 entries per instrument")
         L = _abi.lib()
         rc = L.server_submit(self.h, int(sid), m.ctypes.data, None if j is None else j.ctypes.data, int(tag),
                              float(t_submit))
