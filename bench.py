@@ -606,9 +606,11 @@ def bench_serving(a, rank):
                 if i < len(arrivals):
                     time.sleep(max(0.0, t0 + arrivals[i][0] - api.Server.now()))
         lat = np.array([r["t_done"] - r["t_submit"] for r in res]) * 1e3
+        wait = np.array([r["t_admit"] - r["t_submit"] for r in res]) * 1e3
         span = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
         return {"frames": len(res), "frames_per_s": len(res) / span, "latency_ms_p50": float(np.percentile(lat, 50)),
-                "latency_ms_p99": float(np.percentile(lat, 99)), "ticks": srv.stats()["ticks"]}
+                "latency_ms_p99": float(np.percentile(lat, 99)), "admission_wait_ms_p50": float(np.percentile(wait, 50)),
+                "in_slot_ms_p50": float(np.percentile(lat - wait, 50)), "ticks": srv.stats()["ticks"]}
 
     def plain(realtime: bool):
         opts = [optimiser(x, k) for k, x in enumerate(streams)]
