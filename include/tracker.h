@@ -432,7 +432,7 @@ double server_now(void);
  * streams (each holds a pinned staging copy of max_pixels bytes); max_lambda:
  * largest population of a stream; hbm_reserve_bytes: device memory that
  * server_add_stream must leave free; cluster / threads: launch shape of the
- * fitness launch (0 = 8 CTAs x 256 threads).  Synchronous. */
+ * fitness launch (0 = 4 CTAs x 256 threads).  Synchronous. */
 trk_status server_create(int32_t max_active, int32_t max_streams, int32_t max_pending, int64_t max_pixels,
                          int32_t max_lambda, int64_t hbm_reserve_bytes, int32_t cluster, int32_t threads,
                          trk_server **out);

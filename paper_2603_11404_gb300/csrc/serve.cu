@@ -233,7 +233,7 @@ trk_status server_create(int32_t max_active, int32_t max_streams, int32_t max_pe
     v->reserve = (size_t)hbm_reserve_bytes;
     v->stage_bytes = ((size_t)max_pixels + sizeof(float) * 3 * TRK_MAX_INSTRUMENTS + 255) & ~(size_t)255;
     v->items_cap = (size_t)v->max_active * max_lambda;
-    v->lc.cluster = cluster > 0 ? cluster : 8;
+    v->lc.cluster = cluster > 0 ? cluster : 4;  // 4: one population of 64 fits one wave of the persistent grid
     v->lc.threads = threads > 0 ? threads : 256;
     v->cs.resize(max_streams);
     v->hdescs.resize(max_streams);
