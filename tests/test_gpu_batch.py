@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 import oracle
+from oracle import keypoints as okp
 from paper_2603_11404_gb300 import workload as wl
 
 torch = pytest.importorskip("torch")
@@ -108,3 +109,40 @@ def test_batch_at_the_batching_workload_sizes(api):
     ref = oracle.eval_population(big["sc"], big["P"][[0, 31]], big["M"], n_threads=4)
     c = counts[0].cpu().numpy()[[0, 31]]
     assert np.array_equal(c[:, 0], ref["s"]) and np.array_equal(c[:, 1], ref["I"]) and np.array_equal(c[:, 2], ref["m"])
+
+
+def test_batch_with_filter_and_keypoints_matches_single(api):
+    """Instances with the Kalman filter and the keypoint term switched on (on
+    some instances only): batched frames equal the per-instance frames bit for
+    bit, filtered estimate and covariance included."""
+    inst = _instances(api)
+    frames, pts = (3, 4), (wl.JAW_TIP, wl.JAW_TIP)
+    for k, x in enumerate(inst):
+        if k % 2 == 0:
+            x["tr"].set_keypoints(frames, pts, 3.0, 0.01)
+            tips = okp.project_keypoints(x["sc"], x["gt"].astype(np.float32).astype(np.float64), frames, pts)
+            obs = wl.noisy_detections(tips, x["rng"], sigma_px=2.0, p_invalid=0.0)
+            x["tr"].set_keypoint_obs(torch.from_numpy(obs).cuda())
+
+    def make(i, x):
+        d = x["sc"].d
+        o = api.CMAES(x["tr"], x["lam"], x["gt"] + 0.01, wl.default_scales(d), seed=20 + i, block_diag=d == 18)
+        if i != 1:
+            s = wl.default_scales(d)
+            o.set_filter(1 / 30, (s * 0.5) ** 2, (s * 2.0) ** 2, s ** 2, p_vel0=(s * 10) ** 2, seed_mean=i == 2)
+        return o
+
+    opt_b = [make(i, x) for i, x in enumerate(inst)]
+    opt_s = [make(i, x) for i, x in enumerate(inst)]
+    b = api.Batch([x["tr"] for x in inst], optimisers=opt_b)
+    for frame in range(3):
+        poses = b.track_frame([x["Mp"] for x in inst], 3)
+        torch.cuda.synchronize()
+        for x, o, pb in zip(inst, opt_s, poses):
+            ps = o.track_frame(x["Mp"], 3)
+            torch.cuda.synchronize()
+            assert torch.equal(pb, ps), frame
+    for ob, os_ in zip(opt_b, opt_s):
+        sa, sb = ob.state(), os_.state()
+        assert np.array_equal(sa["C"], sb["C"]) and sa["sigma"] == sb["sigma"]
+        assert np.array_equal(sa["best_x"], sb["best_x"]) and sa["best_loss"] == sb["best_loss"]
