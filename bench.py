@@ -267,12 +267,16 @@ def run_ours(a):
     ops_per_launch = ops / R
     achieved = ops_per_launch / (float(k_ms.mean()) / 1e3)
     peak = _alu_peak()
+    probe = api.probe_int_issue(2000)  # measured integer issue rate of this GPU, outside the timed regions
     traffic = KEVAL_TRAFFIC_BYTES if KEVAL_TRAFFIC_DIGEST == _kernel_digest() else None
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
                 "frac": achieved / peak, "traffic": traffic, "traffic_unit": "DRAM bytes per launch (ncu)",
                 "kernel": "k_eval (fused FK/projection/snap + raster + popcount)",
                 "kernel_ms": float(k_ms.mean()), "ops_per_launch": ops_per_launch,
-                "peak_source": "152 SMs x 64 INT32 ALU lanes/clk x 2070 MHz (derived; LOP3 probe 20.0 Tops/s)"}
+                "peak_source": "152 SMs x 64 INT32 ALU lanes/clk x 2070 MHz (derived)",
+                "peak_probe": probe["tops"], "peak_probe_source": "trk_probe_int_issue: 8 independent LOP3 "
+                "chains per thread, every SM at its thread limit, CUDA events",
+                "frac_of_probe": achieved / (probe["tops"] * 1e12)}
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,

@@ -502,6 +502,19 @@ trk_status cmaes_set_filter(trk_cmaes *es, const trk_filter *f, void *stream);
 trk_status cmaes_save(trk_cmaes *es, void *blob, size_t *n, void *stream);
 trk_status cmaes_load(trk_cmaes *es, const void *blob, size_t n, void *stream);
 
+/* Roofline denominator of the fitness kernel, measured.  The paper has no
+ * counterpart: the fitness path (edge functions, bounding boxes, bit
+ * operations) is bound by integer ALU issue, and this call measures that peak
+ * on the current device.  One kernel fills every SM to its thread limit; each
+ * thread advances eight independent chains of 32-bit LOP3 operations for
+ * iters x 16 steps.  *tops_out = operations / kernel time (CUDA events) in
+ * 10^12 operations per second; *ms_out (may be NULL) the kernel time;
+ * *derived_tops_out (may be NULL) SMs x 64 lanes x the device's maximum SM
+ * clock.  About 4 ms at iters = 2000 on a GB300.  Allocates and frees a small
+ * buffer (4 bytes per thread) and synchronises the device's default stream.
+ * Errors: TRK_EINVAL (iters <= 0, tops_out NULL), TRK_ENOMEM, TRK_ECUDA. */
+trk_status trk_probe_int_issue(int32_t iters, double *tops_out, double *ms_out, double *derived_tops_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -94,6 +94,7 @@ SIGNATURES = {
     "track_frame_host": [P, P, I32, P, P, P, P],
     "cmaes_save": [P, P, P, P],
     "cmaes_load": [P, P, C.c_size_t, P],
+    "trk_probe_int_issue": [I32, P, P, P],
     "eval_population_noalloc": [P, I32, P, I32, P, P, P, P, I32, P, P, P, P],
     "batch_create": [P, P, P, I32, I32, I32, P],
     "batch_destroy": [P],

@@ -193,6 +193,14 @@ def unpack_mask(packed: torch.Tensor, width: int) -> torch.Tensor:
     return u[:, :width].contiguous()
 
 
+def probe_int_issue(iters: int = 2000) -> dict:
+    """trk_probe_int_issue: the measured 32-bit integer issue rate of the current
+    device (the fitness kernel's roofline denominator) and the derived figure."""
+    tops, ms, derived = C.c_double(), C.c_double(), C.c_double()
+    call("trk_probe_int_issue", int(iters), C.byref(tops), C.byref(ms), C.byref(derived))
+    return {"tops": tops.value, "ms": ms.value, "derived_tops": derived.value}
+
+
 class CMAES:
     """Device-resident CMA-ES: cmaes_create / ask / tell / step / track_frame."""
 
