@@ -258,6 +258,7 @@ def run_ours(a):
         kev[i][1].record(stream)
     torch.cuda.synchronize()
     k_ms = np.array([s.elapsed_time(e) for s, e in kev])
+    k_med_ms = max_over_ranks(float(np.median(k_ms)), ws, "cuda")
     # algorithmic work of those launches: 16 ops/vertex, 40 ops/live triangle,
     # 4 ops per pixel of each triangle's screen-clipped bounding box
     ops = 0.0
@@ -293,6 +294,9 @@ def run_ours(a):
                 "d2h_bytes_per_step": 9 * 4 + 4},
         "gpu_launches": a.steps * (1 + GENS),  # per frame: reset + GENS fused generation launches
         "roofline": roofline,
+        "plain_eval": {"evals_per_s": LAM * ws / (k_med_ms / 1e3), "median_us": k_med_ms * 1e3, "launches": R,
+                       "what": "eval_population of one 64-candidate population per launch (fitness only, no "
+                               "CMA-ES update), L2 flushed between launches, CUDA events, median"},
         "tracking_error": {"rot_rad_median": float(np.median(pose_err[:, :3])),
                            "trans_mm_median": float(np.median(pose_err[:, 3:6])),
                            "joint_median": float(np.median(pose_err[:, 6:]))},
