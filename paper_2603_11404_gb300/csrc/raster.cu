@@ -361,17 +361,6 @@ __device__ void raster_warp(const TriSetup &t, uint32_t *bm, int Wq, int lane)
     }
 }
 
-// One thread, int64, any size (overflow of the deferred list).
-__device__ void raster_serial(const TriSetup &t, uint32_t *bm, int Wq)
-{
-    for (int i = t.i0; i <= t.i1; ++i)
-        for (int j = t.j0; j <= t.j1; ++j) {
-            long long Px = 256LL * j, Py = 256LL * i;
-            if ((edge64(t, 0, Px, Py) | edge64(t, 1, Px, Py) | edge64(t, 2, Px, Py)) >= 0)
-                atomicOr(bm + (size_t)i * Wq + (j >> 5), 1u << (j & 31));
-        }
-}
-
 // Camera-frame position of one vertex from its frame's projective rows (hi/lo
 // pairs), perspective division and snap: int2 (U, V) in 1/256 px, or the flag
 // value when the vertex is behind z_near or outside the guard band; uv gets
@@ -491,7 +480,7 @@ __device__ __forceinline__ void eval_candidate(const EvalArgs &a, int c, const u
     uint32_t *bm = reinterpret_cast<uint32_t *>(scr + nI * kComposeScratch);  // [H*Wq]
     float *sM = reinterpret_cast<float *>(bm + ((nwords + 3) & ~3));          // [nI*nF*24]
     int *big = reinterpret_cast<int *>(sM + nI * nF * 24);                    // [kBigListCap]
-    int *sacc = big + kBigListCap;                                            // [8]: s I m culled nbig
+    int *sacc = big + kBigListCap;  // [8]: s I m culled, big-list count, ticket counter, big-list overflow
     __shared__ int red[4][32];
     __shared__ float s_par[kMaxD];
     __shared__ float2 s_z[kMaxD];
@@ -603,9 +592,12 @@ __device__ __forceinline__ void eval_candidate(const EvalArgs &a, int c, const u
                     if (t.spanx < 32 * 256 && t.spany < 64 * 256) {
                         raster_small(t, bm, Wq);
                     } else {
+                        // larger triangles wait for a whole warp; if the list is
+                        // full the CTA redraws every large triangle after the loop
+                        // (no raster code here: it would cost the loop registers)
                         int slot = atomicAdd(&sacc[4], 1);
                         if (slot < kBigListCap) big[slot] = t0;
-                        else raster_serial(t, bm, Wq);
+                        else sacc[6] = 1;
                     }
                 }
             }
@@ -631,6 +623,29 @@ __device__ __forceinline__ void eval_candidate(const EvalArgs &a, int c, const u
         TriSetup t;
         tri_setup(__ldcg(sv + tri.x), __ldcg(sv + tri.y), __ldcg(sv + tri.z), W, H, a.cull, t);
         raster_warp(t, bm, Wq, lane);
+    }
+    if (sacc[6]) {  // the list overflowed: every large triangle of the candidate, a warp each (drawing twice is harmless)
+        for (int base = warp * 32; base < NT; base += nwarp * 32) {
+            const int tt = base + lane;
+            bool large = false;
+            TriSetup t;
+            if (tt < NT) {
+                const int b = tt >= a.T;
+                const int4 tri = a.tris[tt - b * a.T];
+                const int2 *sv = snapc + b * a.V;
+                large = tri_setup(__ldcg(sv + tri.x), __ldcg(sv + tri.y), __ldcg(sv + tri.z), W, H, a.cull, t) == 1 &&
+                        !(t.spanx < 32 * 256 && t.spany < 64 * 256);
+            }
+            for (unsigned mm = __ballot_sync(0xffffffffu, large); mm; mm &= mm - 1) {
+                const int src = __ffs(mm) - 1, tu = __shfl_sync(0xffffffffu, tt, src);
+                const int b = tu >= a.T;
+                const int4 tri = a.tris[tu - b * a.T];
+                const int2 *sv = snapc + b * a.V;
+                TriSetup u;
+                tri_setup(__ldcg(sv + tri.x), __ldcg(sv + tri.y), __ldcg(sv + tri.z), W, H, a.cull, u);
+                raster_warp(u, bm, Wq, lane);
+            }
+        }
     }
     cluster.sync();
 

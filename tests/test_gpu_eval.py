@@ -157,7 +157,8 @@ def test_large_triangles_warp_path(api):
 
 def test_full_screen_quad_and_overflow(api):
     """Two triangles covering all W*H pixel centres, plus many large triangles
-    (more than the deferred-list capacity) to exercise the serial path."""
+    (more than the deferred-list capacity, so the CTA redraws every large
+    triangle after its loop)."""
     W, H, fx, z = 64, 48, 100.0, 100.0
     # corners at pixel (-0.5, -0.5) .. (W-0.5, H-0.5) on the plane z (vertex frame = E, pose t = (0,0,z))
     x0, x1 = (-0.5 - W / 2) * z / fx, (W - 0.5 - W / 2) * z / fx
@@ -177,6 +178,28 @@ def test_full_screen_quad_and_overflow(api):
     M = random_mask(rng, H, W)
     counts, _, _ = _check_population(api, sc, st, M, cluster=1, threads=256)
     assert counts[0, 0] == W * H
+
+
+def test_deferred_list_overflow_draws_every_large_triangle(api):
+    """About 2000 thin triangles 40-60 px wide on one CTA: more than its
+    1024-entry deferred list, so the CTA redraws every large triangle after the
+    loop; the union covers only part of the image, so a triangle left out
+    would change the counts (checked bit for bit against the oracle)."""
+    W, H, fx, z = 512, 256, 100.0, 100.0
+    rng = np.random.default_rng(19)
+    verts, tris = [], []
+    for _ in range(2000):
+        cx_, cy_ = rng.uniform(-W / 2, W / 2), rng.uniform(-H / 2, H / 2)  # px offsets from the centre
+        w_, h_ = rng.uniform(40, 60), rng.uniform(0.5, 2.0)
+        base = len(verts)
+        for dx, dy in ((-w_ / 2, 0.0), (w_ / 2, -h_), (w_ / 2, h_)):
+            verts.append([(cx_ + dx) * z / fx, (cy_ + dy) * z / fx, 0.0])
+        tris.append([base, base + 1, base + 2])
+    sc = tiny_scene(W, H, fx, verts, tris)
+    st = np.array([[0, 0, 0, 0, 0, z, 0, 0, 0], [0, 0, 0.01, 0.3, -0.2, z, 0, 0, 0]], np.float32)
+    M = random_mask(rng, H, W)
+    counts, _, _ = _check_population(api, sc, st, M, cluster=1, threads=256)
+    assert 0.2 * W * H < counts[0, 0] < 0.9 * W * H  # not saturated: every triangle matters
 
 
 def test_all_vertices_flagged_and_nan(api):
