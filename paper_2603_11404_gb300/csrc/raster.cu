@@ -64,14 +64,17 @@ __device__ __forceinline__ dfl rot_entry(int axis, dfl s, dfl c, int i, int j)
 // k = r / t (I + [r]x when t < 1e-8), or look-at Ry(gamma) Rx(alpha) Rz(beta)
 // (Sec. III-A.3).  The lanes run the same code on different data: one
 // sine/cosine evaluation gives the three joint maps and the pose angles,
-// a second one the joint rotations, then the chain products.
-// scr: kComposeScratch float2.
-constexpr int kComposeScratch = 3 + 9 + kMaxFrames * 9 + kMaxFrames * 12;
+// a second one the joint rotations, then the chain products.  The chain's
+// root starts from G = diag(fx, fy, 1) [R | t], so each product down the chain
+// yields the frame's scaled projective rows directly.
+// scr: kComposeScratch float2 (a multiple of two, so what follows stays
+// 16-byte aligned).
+constexpr int kComposeScratch = 4 + 12 + kMaxFrames * 9 + kMaxFrames * 12;
 
 __device__ void compose_frames_warp(const ChainDev &ch, const CamDev &cam, const float *st, float *out,
                                     float2 *scr, int lane)
 {
-    float2 *qs = scr, *Rs = scr + 3, *Js = scr + 12, *Ts = scr + 12 + kMaxFrames * 9;
+    float2 *qs = scr, *G = scr + 4, *Js = scr + 16, *Ts = scr + 16 + kMaxFrames * 9;
     const int nF = ch.n_frames;
     const bool lookat = ch.rot_param == TRK_ROT_LOOKAT;
     const dfl r0 = df_from(st[0]), r1 = df_from(st[1]), r2 = df_from(st[2]);
@@ -144,7 +147,15 @@ __device__ void compose_frames_warp(const ChainDev &ch, const CamDev &cam, const
             Js[9 * lane + e] = make_float2(v.hi, v.lo);
         }
     }
-    if (lane < 9) Rs[lane] = make_float2(Rv.hi, Rv.lo);
+    // G = diag(fx, fy, 1) [R | t], row-major 3 x 4: lanes 0-8 the rotation
+    // entries, lanes 9-11 the translation
+    if (lane < 12) {
+        const int i = lane < 9 ? lane / 3 : lane - 9;
+        dfl g = lane < 9 ? Rv : df_from(st[3 + i]);
+        if (i == 0) g = df_mul(g, dfc(cam.fx_df));
+        if (i == 1) g = df_mul(g, dfc(cam.fy_df));
+        G[lane < 9 ? 4 * i + (lane - 3 * i) : 4 * i + 3] = make_float2(g.hi, g.lo);
+    }
     __syncwarp();
     for (int f = 0; f < nF; ++f) {  // parents first; lane = 4 i + j
         if (lane < 12) {
@@ -153,28 +164,18 @@ __device__ void compose_frames_warp(const ChainDev &ch, const CamDev &cam, const
             dfl L0 = jj < 3 ? dfc(Jf[jj]) : dfc(ch.offset_df[f][0]);
             dfl L1 = jj < 3 ? dfc(Jf[3 + jj]) : dfc(ch.offset_df[f][1]);
             dfl L2 = jj < 3 ? dfc(Jf[6 + jj]) : dfc(ch.offset_df[f][2]);
-            dfl v;
-            if (ch.parent[f] < 0) {
-                v = (i == 0) ? L0 : (i == 1 ? L1 : L2);
-            } else {
-                const float2 *P = Ts + 12 * ch.parent[f];
-                v = dot3(dfc(P[4 * i]), L0, dfc(P[4 * i + 1]), L1, dfc(P[4 * i + 2]), L2);
-                if (jj == 3) v = df_add(v, dfc(P[4 * i + 3]));
-            }
+            const float2 *P = ch.parent[f] < 0 ? G : Ts + 12 * ch.parent[f];
+            dfl v = dot3(dfc(P[4 * i]), L0, dfc(P[4 * i + 1]), L1, dfc(P[4 * i + 2]), L2);
+            if (jj == 3) v = df_add(v, dfc(P[4 * i + 3]));
             Ts[12 * f + lane] = make_float2(v.hi, v.lo);
         }
         __syncwarp();
     }
-    for (int e = lane; e < nF * 12; e += 32) {  // M_f = [R | t] T_f, scaled rows
-        int f = e / 12, r = e - 12 * f, i = r >> 2, jj = r & 3;
-        const float2 *Tf = Ts + 12 * f;
-        dfl v = dot3(dfc(Rs[3 * i]), dfc(Tf[jj]), dfc(Rs[3 * i + 1]), dfc(Tf[4 + jj]), dfc(Rs[3 * i + 2]),
-                     dfc(Tf[8 + jj]));
-        if (jj == 3) v = df_add(v, df_from(st[3 + i]));
-        if (i == 0) v = df_mul(v, dfc(cam.fx_df));
-        if (i == 1) v = df_mul(v, dfc(cam.fy_df));
-        out[24 * f + r] = v.hi;
-        out[24 * f + 12 + r] = v.lo;
+    for (int e = lane; e < nF * 12; e += 32) {  // scaled rows of M_f, hi then lo
+        const int f = e / 12, r = e - 12 * f;
+        const float2 v = Ts[e];
+        out[24 * f + r] = v.x;
+        out[24 * f + 12 + r] = v.y;
     }
     __syncwarp();
 }
@@ -486,7 +487,11 @@ __device__ __forceinline__ void eval_candidate(const EvalArgs &a, int c, const u
     __shared__ float2 s_z[kMaxD];
     __shared__ int s_last;
 
-    for (int w = tid; w < nwords; w += nthr) bm[w] = 0u;
+    {  // the warps that do not compose frames clear the bitmap (16-byte stores)
+        const int c0 = nwarp > nI ? 32 * nI : 0;
+        uint4 *bm4 = reinterpret_cast<uint4 *>(bm);
+        for (int w = tid - c0; w >= 0 && w < (nwords + 3) >> 2; w += nthr - c0) bm4[w] = make_uint4(0u, 0u, 0u, 0u);
+    }
     if (tid < 8) sacc[tid] = 0;
     // ---- prologue: every CTA samples the candidate (fused CMA-ES mode; the
     //      draws are the same in every CTA and CTA 0 stores them) and composes
