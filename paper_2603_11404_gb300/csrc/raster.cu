@@ -362,6 +362,18 @@ __device__ void raster_warp(const TriSetup &t, uint32_t *bm, int Wq, int lane)
     }
 }
 
+// One thread, int64, any size: the batched kernel's fallback when a CTA's
+// deferred list is full.
+__device__ void raster_serial(const TriSetup &t, uint32_t *bm, int Wq)
+{
+    for (int i = t.i0; i <= t.i1; ++i)
+        for (int j = t.j0; j <= t.j1; ++j) {
+            long long Px = 256LL * j, Py = 256LL * i;
+            if ((edge64(t, 0, Px, Py) | edge64(t, 1, Px, Py) | edge64(t, 2, Px, Py)) >= 0)
+                atomicOr(bm + (size_t)i * Wq + (j >> 5), 1u << (j & 31));
+        }
+}
+
 // Camera-frame position of one vertex from its frame's projective rows (hi/lo
 // pairs), perspective division and snap: int2 (U, V) in 1/256 px, or the flag
 // value when the vertex is behind z_near or outside the guard band; uv gets
@@ -463,6 +475,7 @@ cudaError_t launch_project_keypoints(const EvalArgs &a, const float *states, int
 // One candidate c of one evaluation (all CTAs of the cluster call it together).
 // mask_override replaces a.mask when not NULL (batched launches); fused_tell
 // lets the last CTA of the launch run the CMA-ES update (single-instance mode).
+template <bool kInlineFallback>
 __device__ __forceinline__ void eval_candidate(const EvalArgs &a, int c, const uint32_t *mask_override,
                                                bool fused_tell)
 {
@@ -597,11 +610,14 @@ __device__ __forceinline__ void eval_candidate(const EvalArgs &a, int c, const u
                     if (t.spanx < 32 * 256 && t.spany < 64 * 256) {
                         raster_small(t, bm, Wq);
                     } else {
-                        // larger triangles wait for a whole warp; if the list is
-                        // full the CTA redraws every large triangle after the loop
-                        // (no raster code here: it would cost the loop registers)
+                        // larger triangles wait for a whole warp.  If the list is
+                        // full: the plain launch redraws every large triangle after
+                        // the loop (raster code here would make its loop spill); the
+                        // batched launch, compiled with more registers, draws the
+                        // triangle in this lane
                         int slot = atomicAdd(&sacc[4], 1);
                         if (slot < kBigListCap) big[slot] = t0;
+                        else if constexpr (kInlineFallback) raster_serial(t, bm, Wq);
                         else sacc[6] = 1;
                     }
                 }
@@ -629,7 +645,7 @@ __device__ __forceinline__ void eval_candidate(const EvalArgs &a, int c, const u
         tri_setup(__ldcg(sv + tri.x), __ldcg(sv + tri.y), __ldcg(sv + tri.z), W, H, a.cull, t);
         raster_warp(t, bm, Wq, lane);
     }
-    if (sacc[6]) {  // the list overflowed: every large triangle of the candidate, a warp each (drawing twice is harmless)
+    if (!kInlineFallback && sacc[6]) {  // the list overflowed: every large triangle of the candidate, a warp each (drawing twice is harmless)
         for (int base = warp * 32; base < NT; base += nwarp * 32) {
             const int tt = base + lane;
             bool large = false;
@@ -746,7 +762,7 @@ __global__ void __launch_bounds__(256, 4) k_eval(EvalArgs a)
 {
     griddep_launch_dependents();
     griddep_wait();
-    eval_candidate(a, blockIdx.y, nullptr, true);
+    eval_candidate<false>(a, blockIdx.y, nullptr, true);
 }
 
 // Persistent batched evaluation: a fixed grid of clusters pulls (instance,
@@ -770,7 +786,7 @@ __global__ void __launch_bounds__(256, 3) k_eval_batch(const EvalArgs *descs, co
         int4 *dst = reinterpret_cast<int4 *>(&s_args);
         for (int i = threadIdx.x; i < (int)(sizeof(EvalArgs) / 16); i += blockDim.x) dst[i] = src[i];
         __syncthreads();
-        eval_candidate(s_args, ic.y, masks ? masks[ic.x] : nullptr, false);
+        eval_candidate<true>(s_args, ic.y, masks ? masks[ic.x] : nullptr, false);
     }
 }
 

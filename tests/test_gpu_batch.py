@@ -8,6 +8,8 @@ import oracle
 from oracle import keypoints as okp
 from paper_2603_11404_gb300 import workload as wl
 
+from _helpers import random_mask, tiny_scene
+
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
@@ -146,3 +148,30 @@ def test_batch_with_filter_and_keypoints_matches_single(api):
         sa, sb = ob.state(), os_.state()
         assert np.array_equal(sa["C"], sb["C"]) and sa["sigma"] == sb["sigma"]
         assert np.array_equal(sa["best_x"], sb["best_x"]) and sa["best_loss"] == sb["best_loss"]
+
+
+def test_batch_deferred_list_overflow(api):
+    """About 2000 thin triangles 40-60 px wide for one CTA per candidate: its
+    1024-entry deferred list overflows and the batched launch draws the rest in
+    the lanes; counts equal the plain launch's (which the oracle pins) bit for bit."""
+    W, H, fx, z = 512, 256, 100.0, 100.0
+    rng = np.random.default_rng(19)
+    verts, tris = [], []
+    for _ in range(2000):
+        cx_, cy_ = rng.uniform(-W / 2, W / 2), rng.uniform(-H / 2, H / 2)
+        w_, h_ = rng.uniform(40, 60), rng.uniform(0.5, 2.0)
+        base = len(verts)
+        for dx, dy in ((-w_ / 2, 0.0), (w_ / 2, -h_), (w_ / 2, h_)):
+            verts.append([(cx_ + dx) * z / fx, (cy_ + dy) * z / fx, 0.0])
+        tris.append([base, base + 1, base + 2])
+    sc = tiny_scene(W, H, fx, verts, tris)
+    tr = api.Tracker(sc, loss_kind=wl.LOSS_ONE_MINUS_IOU, lambda_max=2, cluster=1, block_threads=256)
+    Mp = tr.pack_mask(torch.from_numpy(random_mask(rng, H, W)).cuda())
+    P = torch.tensor([[0, 0, 0, 0, 0, z, 0, 0, 0], [0, 0, 0.01, 0.3, -0.2, z, 0, 0, 0]], dtype=torch.float32).cuda()
+    b = api.Batch([tr], lams=[2])
+    b.set_launch(1, 256)
+    losses, counts = b.eval([P], [Mp])
+    rl, rc = tr.eval_population(P, Mp, counts=True)
+    torch.cuda.synchronize()
+    assert torch.equal(counts[0], rc) and torch.equal(losses[0].view(torch.int32), rl.view(torch.int32))
+    assert 0.2 * W * H < rc[0, 0].item() < 0.9 * W * H
