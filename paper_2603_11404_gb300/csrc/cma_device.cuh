@@ -238,15 +238,16 @@ static __device__ __noinline__ void onesided_jacobi_smem(float *Xc, float *Jc, i
 // The same with the columns in registers (small compile-time D): lane j holds
 // column j of X and of J, and a round exchanges columns by warp shuffles.
 template <int D>
-__device__ __forceinline__ void onesided_jacobi_regs(float *Xc, float *Jc, int lane, CmaState *st)
+__device__ __forceinline__ void onesided_jacobi_regs(float *Xc, int lane, CmaState *st)
 {
+    // Only the columns are rotated: once they are orthogonal, column j of
+    // X = C B J is C v_j = lambda_j v_j for the eigenvector v_j = (B J)_j, so
+    // the caller recovers the basis by normalising the columns and the
+    // accumulated rotation J is never needed.
     constexpr int N2 = D + (D & 1);
-    float x[D], v[D];
+    float x[D];
 #pragma unroll
-    for (int q = 0; q < D; ++q) {
-        x[q] = lane < D ? Xc[lane * D + q] : 0.0f;
-        v[q] = lane < D ? Jc[lane * D + q] : 0.0f;
-    }
+    for (int q = 0; q < D; ++q) x[q] = lane < D ? Xc[lane * D + q] : 0.0f;
     float amax = 0.0f;
 #pragma unroll
     for (int q = 0; q < D; ++q) amax = fmaxf(amax, x[q] * x[q]);
@@ -266,12 +267,9 @@ __device__ __forceinline__ void onesided_jacobi_regs(float *Xc, float *Jc, int l
             }
             const bool act = lane < D && partner < D;
             const int src = act ? partner : lane;
-            float px[D], pv[D];
+            float px[D];
 #pragma unroll
-            for (int q = 0; q < D; ++q) {
-                px[q] = __shfl_sync(0xffffffffu, x[q], src);
-                pv[q] = __shfl_sync(0xffffffffu, v[q], src);
-            }
+            for (int q = 0; q < D; ++q) px[q] = __shfl_sync(0xffffffffu, x[q], src);
             if (act) {
                 const bool is_lo = lane < partner;
                 float a = 0.0f, b = 0.0f, g = 0.0f;  // |u|^2, |w|^2, u . w with u = lo, w = hi
@@ -290,12 +288,11 @@ __device__ __forceinline__ void onesided_jacobi_regs(float *Xc, float *Jc, int l
                     const float c = rsqrtf(1.0f + t * t), sn = t * c;
                     rotated = true;
                     rho = fmaxf(rho, fabsf(g) * rsqrtf(a * b));
+                    const float cu = is_lo ? c : sn, cw = is_lo ? -sn : c;  // own = cu u + cw w
 #pragma unroll
                     for (int q = 0; q < D; ++q) {
                         const float u = is_lo ? x[q] : px[q], w = is_lo ? px[q] : x[q];
-                        const float ju = is_lo ? v[q] : pv[q], jw = is_lo ? pv[q] : v[q];
-                        x[q] = is_lo ? fmaf(c, u, -sn * w) : fmaf(sn, u, c * w);
-                        v[q] = is_lo ? fmaf(c, ju, -sn * jw) : fmaf(sn, ju, c * jw);
+                        x[q] = fmaf(cu, u, cw * w);
                     }
                 }
             }
@@ -308,10 +305,7 @@ __device__ __forceinline__ void onesided_jacobi_regs(float *Xc, float *Jc, int l
     }
     if (lane < D)
 #pragma unroll
-        for (int q = 0; q < D; ++q) {
-            Xc[lane * D + q] = x[q];
-            Jc[lane * D + q] = v[q];
-        }
+        for (int q = 0; q < D; ++q) Xc[lane * D + q] = x[q];
     if (lane == 0) st->jacobi_sweeps = sweeps;
     __syncwarp();
 }
@@ -454,12 +448,14 @@ __device__ __forceinline__ void cma_tell_impl(const CmaConst &k, CmaState *st, c
     //      the columns of X = C B (B = last generation's basis, a warm start),
     //      one warp, columns in shared memory.  Each round pairs the columns by
     //      the circle method; a pair (u, w) is rotated by the angle that makes
-    //      u . w = 0, cot 2 theta = (|w|^2 - |u|^2) / (2 u . w), and the same
-    //      rotation is applied to the accumulated basis J.  When every pair has
-    //      |u . w| <= 1e-5 |u| |w| the columns of C B J are orthogonal to that
-    //      level, so B J is an eigenbasis of C up to off-diagonal terms of
-    //      V^T C V below 1e-5 of the diagonal, which the FP64 square-root
-    //      refinement absorbs (its error is of third order in them) ----
+    //      u . w = 0, cot 2 theta = (|w|^2 - |u|^2) / (2 u . w).  When every
+    //      pair has |u . w| <= 1e-5 |u| |w| the columns of C B J are orthogonal
+    //      to that level, so B J is an eigenbasis of C up to off-diagonal terms
+    //      of V^T C V below 1e-5 of the diagonal, which the FP64 square-root
+    //      refinement absorbs (its error is of third order in them).  Column j
+    //      of C B J is then lambda_j (B J)_j: with the columns in registers
+    //      (d <= 12) the basis is the normalised columns; the shared-memory
+    //      form (d = 18) accumulates J alongside ----
     for (int e = tid; e < dd; e += nt) {
         const int i = e / d, j = e - i * d;
         float acc = 0.0f;
@@ -468,9 +464,10 @@ __device__ __forceinline__ void cma_tell_impl(const CmaConst &k, CmaState *st, c
         S.Vf2[j * d + i] = (i == j) ? 1.0f : 0.0f;  // column j of J
     }
     __syncthreads();
+    constexpr bool kRegs = DC > 0 && DC <= 12;  // columns in registers, basis from the columns
     if (tid < 32) {
-        if constexpr (DC > 0 && DC <= 12)
-            onesided_jacobi_regs<DC>(S.Af, S.Vf2, tid, st);
+        if constexpr (kRegs)
+            onesided_jacobi_regs<DC>(S.Af, tid, st);
         else
             onesided_jacobi_smem<DC>(S.Af, S.Vf2, d, tid, st);
     }
@@ -483,20 +480,33 @@ __device__ __forceinline__ void cma_tell_impl(const CmaConst &k, CmaState *st, c
         st->gen_total += 1;
     }
     __syncthreads();
-    for (int e = tid; e < dd; e += nt) {  // J row-major for phase 2
-        const int i = e / d, j = e - i * d;
-        S.Vf[e] = S.Vf2[j * d + i];
-    }
-    __syncthreads();
-    const float *Vf = S.Vf;
-    // ---- phase 2: V = orth(B Vf) in FP64 (two Newton-Schulz polar steps,
-    //      V <- V (3 I - V^T V) / 2, taking 1e-6 to FP64 rounding) ----
+    // ---- phase 2: V = orth(B J) in FP64 (two Newton-Schulz polar steps,
+    //      V <- V (3 I - V^T V) / 2, taking 1e-6 to FP64 rounding); B J is the
+    //      normalised columns of X (register path) or B times the accumulated J ----
     double *V = S.V, *V2 = S.V2, *A = S.A, *A2 = S.A2;
-    for (int e = tid; e < dd; e += nt) {
-        int i = e / d, j = e - i * d;
-        double acc = 0.0;
-        for (int q = 0; q < d; ++q) acc = __fma_rn(S.B[i * d + q], (double)Vf[q * d + j], acc);
-        V[e] = acc;
+    if constexpr (kRegs) {
+        if (tid < d) {  // 1 / |x_j| for column j
+            double n2 = 0.0;
+            for (int q = 0; q < d; ++q) n2 = __fma_rn((double)S.Af[tid * d + q], (double)S.Af[tid * d + q], n2);
+            S.part[0][tid] = rsqrt(n2);
+        }
+        __syncthreads();
+        for (int e = tid; e < dd; e += nt) {
+            int i = e / d, j = e - i * d;
+            V[e] = (double)S.Af[j * d + i] * S.part[0][j];
+        }
+    } else {
+        for (int e = tid; e < dd; e += nt) {  // J row-major
+            const int i = e / d, j = e - i * d;
+            S.Vf[e] = S.Vf2[j * d + i];
+        }
+        __syncthreads();
+        for (int e = tid; e < dd; e += nt) {
+            int i = e / d, j = e - i * d;
+            double acc = 0.0;
+            for (int q = 0; q < d; ++q) acc = __fma_rn(S.B[i * d + q], (double)S.Vf[q * d + j], acc);
+            V[e] = acc;
+        }
     }
     __syncthreads();
     for (int step = 0; step < 2; ++step) {
