@@ -475,9 +475,17 @@ cudaError_t launch_project_keypoints(const EvalArgs &a, const float *states, int
 // One candidate c of one evaluation (all CTAs of the cluster call it together).
 // mask_override replaces a.mask when not NULL (batched launches); fused_tell
 // lets the last CTA of the launch run the CMA-ES update (single-instance mode).
+// Programmatic dependent launch: consecutive fused generations are launched
+// with programmatic stream serialisation, so the next generation's CTAs may be
+// scheduled while this one is still running (its last CTA runs the update);
+// they wait for this grid to complete, memory included, before reading
+// anything.  Without that launch attribute both instructions do nothing.
+__device__ __forceinline__ void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;"); }
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 template <bool kInlineFallback>
 __device__ __forceinline__ void eval_candidate(const EvalArgs &a, int c, const uint32_t *mask_override,
-                                               bool fused_tell)
+                                               bool fused_tell, bool dependent_launch)
 {
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
@@ -506,6 +514,9 @@ __device__ __forceinline__ void eval_candidate(const EvalArgs &a, int c, const u
         for (int w = tid - c0; w >= 0 && w < (nwords + 3) >> 2; w += nthr - c0) bm4[w] = make_uint4(0u, 0u, 0u, 0u);
     }
     if (tid < 8) sacc[tid] = 0;
+    // everything above touches only this CTA's shared memory; from here on the
+    // launch reads what the previous generation wrote
+    if (dependent_launch) griddep_wait();
     // ---- prologue: every CTA samples the candidate (fused CMA-ES mode; the
     //      draws are the same in every CTA and CTA 0 stores them) and composes
     //      its frames in double-float, so no CTA waits for another ----
@@ -750,19 +761,10 @@ __device__ __forceinline__ void eval_candidate(const EvalArgs &a, int c, const u
     }
 }
 
-// Programmatic dependent launch: consecutive fused generations are launched
-// with programmatic stream serialisation, so the next generation's CTAs may be
-// scheduled while this one is still running (its last CTA runs the update);
-// they wait for this grid to complete, memory included, before reading
-// anything.  Without that launch attribute both instructions do nothing.
-__device__ __forceinline__ void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;"); }
-__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-
 __global__ void __launch_bounds__(256, 4) k_eval(EvalArgs a)
 {
     griddep_launch_dependents();
-    griddep_wait();
-    eval_candidate<false>(a, blockIdx.y, nullptr, true);
+    eval_candidate<false>(a, blockIdx.y, nullptr, true, true);
 }
 
 // Persistent batched evaluation: a fixed grid of clusters pulls (instance,
@@ -786,7 +788,7 @@ __global__ void __launch_bounds__(256, 3) k_eval_batch(const EvalArgs *descs, co
         int4 *dst = reinterpret_cast<int4 *>(&s_args);
         for (int i = threadIdx.x; i < (int)(sizeof(EvalArgs) / 16); i += blockDim.x) dst[i] = src[i];
         __syncthreads();
-        eval_candidate<true>(s_args, ic.y, masks ? masks[ic.x] : nullptr, false);
+        eval_candidate<true>(s_args, ic.y, masks ? masks[ic.x] : nullptr, false, false);
     }
 }
 
