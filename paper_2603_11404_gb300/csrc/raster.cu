@@ -64,8 +64,9 @@ __device__ __forceinline__ dfl rot_entry(int axis, dfl s, dfl c, int i, int j)
 // k = r / t (I + [r]x when t < 1e-8), or look-at Ry(gamma) Rx(alpha) Rz(beta)
 // (Sec. III-A.3).  The lanes run the same code on different data: one
 // sine/cosine evaluation gives the three joint maps and the pose angles,
-// a second one the joint rotations, then the chain products.  The chain's
-// root starts from G = diag(fx, fy, 1) [R | t], so each product down the chain
+// a second one the joint rotations, then the chain products, level by level
+// (frames at the same distance from the root in parallel).  The chain's root
+// starts from G = diag(fx, fy, 1) [R | t], so each product down the chain
 // yields the frame's scaled projective rows directly.
 // scr: kComposeScratch float2 (a multiple of two, so what follows stays
 // 16-byte aligned).
@@ -157,19 +158,34 @@ __device__ void compose_frames_warp(const ChainDev &ch, const CamDev &cam, const
         G[lane < 9 ? 4 * i + (lane - 3 * i) : 4 * i + 3] = make_float2(g.hi, g.lo);
     }
     __syncwarp();
-    for (int f = 0; f < nF; ++f) {  // parents first; lane = 4 i + j
-        if (lane < 12) {
-            int i = lane >> 2, jj = lane & 3;
-            const float2 *Jf = Js + 9 * f;
-            dfl L0 = jj < 3 ? dfc(Jf[jj]) : dfc(ch.offset_df[f][0]);
-            dfl L1 = jj < 3 ? dfc(Jf[3 + jj]) : dfc(ch.offset_df[f][1]);
-            dfl L2 = jj < 3 ? dfc(Jf[6 + jj]) : dfc(ch.offset_df[f][2]);
-            const float2 *P = ch.parent[f] < 0 ? G : Ts + 12 * ch.parent[f];
-            dfl v = dot3(dfc(P[4 * i]), L0, dfc(P[4 * i + 1]), L1, dfc(P[4 * i + 2]), L2);
-            if (jj == 3) v = df_add(v, dfc(P[4 * i + 3]));
-            Ts[12 * f + lane] = make_float2(v.hi, v.lo);
+    // the chain, level by level (a frame's level is its distance from the root):
+    // the frames of one level are independent, two at a time (12 lanes each,
+    // lane = 4 i + j within a frame)
+    int lvl = 0;
+    if (lane < nF)
+        for (int q = ch.parent[lane]; q >= 0; q = ch.parent[q]) ++lvl;
+    int top = lvl;
+    for (int o = 16; o; o >>= 1) top = max(top, __shfl_xor_sync(0xffffffffu, top, o));
+    for (int l = 0; l <= top; ++l) {
+        for (unsigned fm = __ballot_sync(0xffffffffu, lane < nF && lvl == l); fm;) {
+            const int fa = __ffs(fm) - 1;
+            fm &= fm - 1;
+            const int fb = fm ? __ffs(fm) - 1 : -1;
+            if (fm) fm &= fm - 1;
+            const int f = lane < 12 ? fa : (lane < 24 ? fb : -1);
+            if (f >= 0) {
+                const int e = lane < 12 ? lane : lane - 12, i = e >> 2, jj = e & 3;
+                const float2 *Jf = Js + 9 * f;
+                dfl L0 = jj < 3 ? dfc(Jf[jj]) : dfc(ch.offset_df[f][0]);
+                dfl L1 = jj < 3 ? dfc(Jf[3 + jj]) : dfc(ch.offset_df[f][1]);
+                dfl L2 = jj < 3 ? dfc(Jf[6 + jj]) : dfc(ch.offset_df[f][2]);
+                const float2 *P = ch.parent[f] < 0 ? G : Ts + 12 * ch.parent[f];
+                dfl v = dot3(dfc(P[4 * i]), L0, dfc(P[4 * i + 1]), L1, dfc(P[4 * i + 2]), L2);
+                if (jj == 3) v = df_add(v, dfc(P[4 * i + 3]));
+                Ts[12 * f + e] = make_float2(v.hi, v.lo);
+            }
+            __syncwarp();
         }
-        __syncwarp();
     }
     for (int e = lane; e < nF * 12; e += 32) {  // scaled rows of M_f, hi then lo
         const int f = e / 12, r = e - 12 * f;
