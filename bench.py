@@ -42,8 +42,8 @@ ALGO_OPS_PER_VERT, ALGO_OPS_PER_TRI, ALGO_OPS_PER_BBOX_PX = 16, 40, 4
 # DRAM bytes (read + write) of one plain k_eval launch at 640x512, lambda = 64, from
 # ncu (profiles/k_eval_640x512.md), valid for the kernel sources with this digest;
 # reported as null once those sources change.
-KEVAL_TRAFFIC_BYTES = 606464
-KEVAL_TRAFFIC_DIGEST = "fcc00638b20e903e"
+KEVAL_TRAFFIC_BYTES = 606976
+KEVAL_TRAFFIC_DIGEST = "6c589f918eb2d341"
 KERNEL_SOURCES = ("raster.cu", "cma_device.cuh", "df.cuh", "internal.cuh")
 
 
