@@ -124,6 +124,25 @@ def test_bimanual_and_ragged_image(api):
     _check_population(api, sc, P, M, wl.LOSS_ONE_MINUS_IOU, lambda_max=9)
 
 
+def test_branched_chain_matches_oracle(api):
+    """A chain other than the instrument's: eight frames whose levels (distance
+    from a root) hold 2, 2, 3 and 1 frames, so the level-by-level composition
+    takes two passes on one level; a small mesh on every frame."""
+    F = wl.Frame
+    frames = [F(-1, (0.0, 0.0, 0.0)), F(-1, (0.0, 0.0, 0.0), 1, 0, 1.0), F(1, (0.0, 0.0, 9.0), 2, 1, 1.0),
+              F(2, (3.0, 0.0, 2.0), 2, 2, 0.5), F(2, (-3.0, 0.0, 2.0), 2, 2, -0.5), F(2, (0.0, 3.0, 2.0), 3, 2, 1.0),
+              F(3, (0.0, 0.0, 4.0), 1, 1, 0.7), F(1, (0.0, 4.0, 0.0))]
+    meshes = [wl.shaft_mesh(0, length=60.0, rings=6)] + [wl.box_mesh(f, 3.0, 2.0, 4.0, div=(1, 1, 2)) for f in range(1, 8)]
+    K = wl.Intrinsics(200.0, 200.0, 80.0, 64.0, 160, 128)
+    sc = wl.Scene(frames, meshes, wl.Q_LB.copy(), wl.Q_UB.copy(), K)
+    rng = np.random.default_rng(17)
+    gt = wl.sample_state(rng, K)
+    M = wl.corrupt_mask(oracle.render(sc, gt), rng)
+    assert M.sum() > 200
+    P = wl.population_around(rng, gt, 6)
+    _check_population(api, sc, P, M, wl.LOSS_ONE_MINUS_IOU)
+
+
 def test_single_candidate_and_cull_mode(api):
     sc = wl.make_scene("c1", "c1")
     rng = np.random.default_rng(6)
