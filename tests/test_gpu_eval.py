@@ -152,7 +152,7 @@ def test_single_candidate_and_cull_mode(api):
     _check_population(api, sc, P, M, cull=True)
 
 
-@pytest.mark.parametrize("cluster,threads", [(1, 64), (2, 128), (8, 256), (3, 96)])
+@pytest.mark.parametrize("cluster,threads", [(1, 32), (1, 64), (2, 128), (8, 256), (3, 96)])
 def test_launch_shapes_agree(api, cluster, threads):
     sc = wl.make_scene("c1", "c1")
     rng = np.random.default_rng(7)
@@ -160,6 +160,19 @@ def test_launch_shapes_agree(api, cluster, threads):
     M = oracle.render(sc, gt)
     P = wl.population_around(rng, gt, 5)
     _check_population(api, sc, P, M, cluster=cluster, threads=threads)
+
+
+@pytest.mark.parametrize("cluster,threads", [(1, 64), (4, 64), (2, 96)])
+def test_bimanual_launch_shapes_agree(api, cluster, threads):
+    """Two instruments with one or two warps beyond the composing ones (with
+    64 threads every warp composes and also clears the bitmap)."""
+    K = wl.Intrinsics(150.0, 150.0, 50.0, 38.5, 101, 77)
+    sc = wl.make_scene("c1", "c1", n_instruments=2, K=K)
+    rng = np.random.default_rng(27)
+    gt = np.concatenate([wl.sample_state(rng, K), wl.sample_state(rng, K)])
+    M = wl.corrupt_mask(oracle.render(sc, gt), rng)
+    P = wl.population_around(rng, gt, 4)
+    _check_population(api, sc, P, M, wl.LOSS_ONE_MINUS_IOU, cluster=cluster, threads=threads)
 
 
 def test_large_triangles_warp_path(api):
