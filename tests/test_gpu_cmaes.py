@@ -205,14 +205,19 @@ def test_multi_frame_warm_start(api):
     assert np.mean(lg_all) <= 1.5 * np.mean(lo_all) + 20
 
 
-@pytest.mark.parametrize("scene_kw,lam", [({"mesh": "c1", "cam": "c1"}, 16),
-                                          ({"mesh": "c1", "cam": "c1", "n_instruments": 2}, 32)])
-def test_fused_generation_equals_separate_calls(api, scene_kw, lam):
+@pytest.mark.parametrize("scene_kw,lam,shape", [({"mesh": "c1", "cam": "c1"}, 16, (0, 0)),
+                                                ({"mesh": "c1", "cam": "c1", "n_instruments": 2}, 32, (0, 0)),
+                                                ({"mesh": "c1", "cam": "c1"}, 16, (2, 32)),
+                                                ({"mesh": "c1", "cam": "c1"}, 24, (8, 64)),
+                                                ({"mesh": "c1", "cam": "c1", "n_instruments": 2}, 16, (1, 64))])
+def test_fused_generation_equals_separate_calls(api, scene_kw, lam, shape):
     """cmaes_step (sample + fitness + update in one launch) is bit-identical to
-    cmaes_ask, eval_population and cmaes_tell issued separately."""
+    cmaes_ask, eval_population and cmaes_tell issued separately, whatever the
+    launch shape (the fused update runs with the fitness CTA's threads: with 32
+    threads the step-size update follows the Jacobi pass on the same warp)."""
     sc = wl.make_scene(**scene_kw)
     d = sc.d
-    tr = api.Tracker(sc, loss_kind=wl.LOSS_ONE_MINUS_IOU, lambda_max=lam)
+    tr = api.Tracker(sc, loss_kind=wl.LOSS_ONE_MINUS_IOU, lambda_max=lam, cluster=shape[0], block_threads=shape[1])
     rng = np.random.default_rng(31)
     gt = np.concatenate([wl.sample_state(rng, sc.K) for _ in range(sc.n_instruments)])
     M = wl.corrupt_mask(oracle.render(sc, gt), rng)
