@@ -18,9 +18,18 @@ from ._abi import call
 LOSS_XOR, LOSS_ONE_MINUS_IOU, LOSS_MSE_APP = 0, 1, 2
 
 
+# the current stream's handle in one call each (torch.cuda.current_stream()
+# builds a Stream object per call, a noticeable share of a frame's host time)
+_raw_stream = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+_cur_device = getattr(torch._C, "_cuda_getDevice", None)
+
+
 def _stream(stream=None):
-    s = stream if stream is not None else torch.cuda.current_stream()
-    return C.c_void_p(s.cuda_stream)
+    if stream is not None:
+        return C.c_void_p(stream.cuda_stream)
+    if _raw_stream is not None and _cur_device is not None:
+        return C.c_void_p(_raw_stream(_cur_device()))
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
 def _ptr(t):
@@ -216,6 +225,9 @@ class CMAES:
         call("cmaes_create", tracker.h, self.lam, _ptr(mean), _ptr(scales), float(sigma0), int(seed) & (2 ** 64 - 1),
              int(stream_id), int(bool(block_diag)), C.byref(h))
         self.h = h
+        K = tracker.scene.K
+        self._hw = (K.height, K.width)
+        self._tfh = _abi.lib().track_frame_host
 
     def close(self):
         if getattr(self, "h", None):
@@ -279,19 +291,28 @@ class CMAES:
         return pose_out
 
     def track_frame_host(self, mask_u8, generations: int, joint_reading=None, stream=None):
-        """track_frame_host: host mask [H, W] uint8 (numpy or pinned tensor) -> (pose [d], best loss)."""
+        """track_frame_host: host mask [H, W] uint8 (numpy or pinned tensor) -> (pose [d], best loss).
+        Kept lean: it runs once per camera frame, so its host time is part of every frame's latency."""
         if isinstance(mask_u8, torch.Tensor):
-            assert not mask_u8.is_cuda and mask_u8.dtype == torch.uint8 and mask_u8.is_contiguous()
+            if mask_u8.is_cuda or mask_u8.dtype != torch.uint8 or not mask_u8.is_contiguous():
+                raise ValueError("mask must be a contiguous host uint8 tensor")
+            mp = mask_u8.data_ptr()
         else:
             mask_u8 = np.ascontiguousarray(mask_u8, np.uint8)
-        K = self.tracker.scene.K
-        if tuple(mask_u8.shape) != (K.height, K.width):
-            raise ValueError(f"mask must be [{K.height}, {K.width}] uint8")
-        pose = np.zeros(self.d, np.float32)
+            mp = mask_u8.ctypes.data
+        if tuple(mask_u8.shape) != self._hw:
+            raise ValueError(f"mask must be [{self._hw[0]}, {self._hw[1]}] uint8")
+        pose = np.empty(self.d, np.float32)
         bl = C.c_float()
-        jr = None if joint_reading is None else np.ascontiguousarray(joint_reading, np.float32)
-        call("track_frame_host", self.h, _ptr(mask_u8), int(generations), _ptr(jr), _ptr(pose), C.byref(bl),
-             _stream(stream))
+        jp = None
+        if joint_reading is not None:
+            jr = np.ascontiguousarray(joint_reading, np.float32)
+            if jr.size < 3 * self.tracker.scene.n_instruments:
+                raise ValueError("joint reading needs 3 values per instrument")
+            jp = jr.ctypes.data
+        rc = self._tfh(self.h, mp, int(generations), jp, pose.ctypes.data, C.byref(bl), _stream(stream))
+        if rc:
+            raise _abi.TrkError(rc, "track_frame_host", _abi.lib().tracker_last_error().decode(errors="replace"))
         return pose, bl.value
 
     def set_filter(self, dt: float, q_pos, q_vel, r, p_vel0=None, seed_mean: bool = True, enabled: bool = True,
