@@ -694,9 +694,41 @@ def cpu_baseline(seconds: float):
         if time.perf_counter() - t0 > seconds:
             break
     el = time.perf_counter() - t0
+    # the same oracle on one thread, a shorter bounded sample
+    n1, t1, g = 0, time.perf_counter(), 0
+    while True:
+        M = _corrupt(oracle.render(sc, traj[g % 64]), 0, g % 64)
+        P = wl.population_around(rng, traj[g % 64], LAM)
+        oracle.eval_population(sc, P, M, n_threads=1)
+        n1 += LAM
+        g += 1
+        if time.perf_counter() - t1 > max(1.0, seconds / 3):
+            break
+    el1 = time.perf_counter() - t1
     return {"value": n / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{f} populations of {LAM} candidates (640x512, {sc.n_tris} triangles), "
-                      f"oracle renderer + counts over {cores} threads, {el:.1f} s incl. mask setup"}
+                      f"oracle renderer + counts over {cores} threads, {el:.1f} s incl. mask setup",
+            "value_1thread": n1 / el1, "sample_1thread": f"{g} populations on one thread, {el1:.1f} s",
+            "cpu_model": _cpu_model()}
+
+
+def _cpu_model():
+    """The host CPU as /proc/cpuinfo names it (model name, or the Arm part number)."""
+    import platform
+    try:
+        fields = {}
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    fields.setdefault(k.strip(), v.strip())
+        if "model name" in fields:
+            return fields["model name"]
+        if "CPU part" in fields:
+            return f"{platform.machine()} (implementer {fields.get('CPU implementer', '?')}, part {fields['CPU part']})"
+    except OSError:
+        pass
+    return platform.machine()
 
 
 def run_reference(a):
