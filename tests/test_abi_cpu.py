@@ -52,3 +52,13 @@ def test_host_side_argument_checks(lib):
     assert lib.trk_probe_int_issue(0, C.byref(tops), None, None) == TRK_EINVAL
     assert b"iters" in lib.tracker_last_error()
     assert lib.trk_probe_int_issue(100, None, None, None) == TRK_EINVAL
+
+
+def test_image_above_the_bitmap_limit_is_rejected(lib):
+    """One row more than TRK_MAX_PIXELS (1280 x 1280: the bitmap must fit one
+    CTA's shared memory) is refused by tracker_create before any allocation."""
+    from paper_2603_11404_gb300 import api, workload as wl
+    K = wl.Intrinsics(1600.0, 1600.0, 640.0, 640.5, 1280, 1281)
+    with pytest.raises(_abi.TrkError) as e:
+        api.Tracker(wl.make_scene("c1", "c1", K=K), lambda_max=4)
+    assert e.value.status == TRK_EINVAL

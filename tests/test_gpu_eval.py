@@ -143,6 +143,19 @@ def test_branched_chain_matches_oracle(api):
     _check_population(api, sc, P, M, wl.LOSS_ONE_MINUS_IOU)
 
 
+def test_largest_image(api):
+    """1280 x 1280, the largest image a tracker takes (a 200 KB bitmap per CTA),
+    with the 5000-triangle mesh close to the camera."""
+    K = wl.Intrinsics(1600.0, 1600.0, 640.0, 640.0, 1280, 1280)
+    sc = wl.make_scene("5000", "c1", K=K)
+    rng = np.random.default_rng(37)
+    gt = wl.sample_state(rng, K, z_range=(60.0, 90.0))
+    M = wl.corrupt_mask(oracle.render(sc, gt), rng)
+    P = wl.population_around(rng, gt, 3)
+    counts, _, _ = _check_population(api, sc, P, M, wl.LOSS_ONE_MINUS_IOU)
+    assert counts[:, 0].min() > 10000
+
+
 def test_single_candidate_and_cull_mode(api):
     sc = wl.make_scene("c1", "c1")
     rng = np.random.default_rng(6)
