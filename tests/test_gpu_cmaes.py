@@ -29,8 +29,12 @@ def _quadratic_loss(P, target, wts):
     return (((P.astype(np.float64) - target) ** 2) @ wts).astype(np.float32)
 
 
-@pytest.mark.parametrize("d,lam,block", [(9, 16, False), (9, 64, False), (18, 64, True), (18, 32, False)])
+@pytest.mark.parametrize("d,lam,block", [(9, 16, False), (9, 64, False), (18, 64, True), (18, 32, False),
+                                         (9, 1024, False), (18, 256, True)])
 def test_ask_tell_state_parity(api, d, lam, block):
+    """Against the FP64 oracle CMA-ES fed the same normals.  The last two
+    populations are large enough that the update reads the selected steps from
+    global memory instead of staging them in shared memory."""
     n_inst = d // 9
     sc = wl.make_scene("c1", "c1", n_instruments=n_inst)
     tr = api.Tracker(sc, lambda_max=lam)
@@ -56,11 +60,11 @@ def test_ask_tell_state_parity(api, d, lam, block):
         o.tell(loss)
         st = g.state()
         assert st["gen"] == o.gen and st["gen_total"] == o.gen_total
-        # The device eigendecomposition is accurate to ~1e-12 relative (FP64
-        # Jacobi sweeps after the FP32 pass until no off-diagonal entry exceeds
-        # 1e-11 of the largest diagonal one).  Perturbing the oracle's C by
-        # 1e-12 relative before every decomposition moves its state by ~1e-11
-        # after 25 generations, so 1e-9 leaves a wide margin.
+        # The device square roots are accurate to ~1e-12 relative (an FP32
+        # Jacobi pass, then Newton-Schulz orthogonalisation and Newton
+        # square-root steps in FP64).  Perturbing the oracle's C by 1e-12
+        # relative before every decomposition moves its state by ~1e-11 after
+        # 25 generations, so 1e-9 leaves a wide margin.
         assert _rel(st["m"], o.m) < 1e-9
         assert abs(st["sigma"] - o.sigma) / o.sigma < 1e-9
         assert _rel(st["C"], o.C) < 1e-9
@@ -69,7 +73,7 @@ def test_ask_tell_state_parity(api, d, lam, block):
         if block:
             assert np.all(st["C"][:9, 9:] == 0) and np.all(st["C"][9:, :9] == 0)
         assert np.array_equal(st["C"], st["C"].T)
-    assert n_ulp_diff <= 3
+    assert n_ulp_diff <= 3 + lam * d * 25 // 5000  # one-ulp sampling differences at rounding ties are rare
 
 
 @pytest.mark.parametrize("d,lam", [(9, 64), (18, 32)])
