@@ -248,8 +248,9 @@ trk_status cmaes_last_normals(trk_cmaes *es, double *z_dev, void *stream);
 /* Update from loss_dev [lam] (lower is better; NaN ranks last) for the
  * population of the last ask: stable ranking by (loss, index), weighted
  * recombination, p_sigma, p_c, rank-one and rank-mu update of C, cumulative
- * step-size adaptation, and an FP64 Jacobi eigendecomposition of C (warm-
- * started from the previous eigenbasis) giving C^(1/2) and C^(-1/2).
+ * step-size adaptation, and C^(1/2), C^(-1/2) from an eigenbasis of C warm-
+ * started from the previous one (an FP32 one-sided Jacobi pass, then FP64
+ * Newton-Schulz orthogonalisation and two Newton steps for the square root).
  * Asynchronous. */
 trk_status cmaes_tell(trk_cmaes *es, const float *loss_dev, void *stream);
 
