@@ -121,7 +121,10 @@ const char *tracker_last_error(void);
 
 /* Create a tracker on the current CUDA device: validates and copies the link
  * meshes, the chain and the intrinsics to the device and allocates the
- * per-candidate scratch (snapped vertices) for lambda_max candidates.
+ * per-candidate scratch (snapped vertices) for lambda_max candidates.  Every
+ * fitness launch on the tracker uses that scratch, so launches that could
+ * overlap on the GPU (other streams, other host threads) race on it: issue
+ * them on one stream, or order them with events.
  * Errors: TRK_EINVAL for out-of-range indices, frames, sizes, non-integer
  * 256*cx, images larger than TRK_MAX_PIXELS; TRK_ENOMEM; TRK_ECUDA.
  * Sec. III-A.2 (renderer inputs: v_m, T_m^r, K). */
