@@ -65,6 +65,18 @@ typedef enum {
 enum { TRK_AXIS_NONE = 0, TRK_AXIS_X = 1, TRK_AXIS_Y = 2, TRK_AXIS_Z = 3 };
 enum { TRK_ROT_AXIS_ANGLE = 0, TRK_ROT_LOOKAT = 1 };
 enum { TRK_LOSS_XOR = 0, TRK_LOSS_ONE_MINUS_IOU = 1, TRK_LOSS_MSE_APP = 2 };
+/* Rasteriser of the fitness path (trk_config.raster); both give identical counts.
+ *  CLUSTER: one thread-block cluster per candidate draws every triangle into
+ *           per-CTA full-image bitmaps in shared memory, OR-ed through
+ *           distributed shared memory (images up to TRK_MAX_PIXELS).
+ *  BINNED:  a cluster per candidate projects, sets up and bins the live
+ *           triangles by 64 x 32-pixel screen tile (an exact counting sort);
+ *           a persistent grid then rasterises the bins in chunks of 256
+ *           triangles into shared-memory tile bitmaps and popcounts them
+ *           against the mask (images up to 16384 x 8192).
+ *  AUTO:    CLUSTER (the faster on every workload measured), BINNED only
+ *           where the full-image bitmap would not fit one CTA's shared memory. */
+enum { TRK_RASTER_AUTO = 0, TRK_RASTER_CLUSTER = 1, TRK_RASTER_BINNED = 2 };
 
 /* One rigid link mesh in the coordinates of kinematic frame `frame`
  * (the CAD vertices v_m of Sec. III-A.2).  Host arrays, copied at create. */
@@ -109,6 +121,7 @@ typedef struct {
     int32_t cluster;       /* CTAs per candidate, 1..8 (0 = auto)                */
     int32_t block_threads; /* threads per CTA: multiple of 32, >= 32 per instrument,
                               <= 256 (0 = auto)                                  */
+    int32_t raster;        /* TRK_RASTER_* (0 = auto)                            */
 } trk_config;
 
 typedef struct trk_tracker trk_tracker;

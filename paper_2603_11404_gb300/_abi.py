@@ -48,7 +48,8 @@ class Intrinsics(C.Structure):
 
 class Config(C.Structure):
     _fields_ = [("loss_kind", C.c_int32), ("lambda_app", C.c_float), ("cull_backfaces", C.c_int32),
-                ("lambda_max", C.c_int32), ("cluster", C.c_int32), ("block_threads", C.c_int32)]
+                ("lambda_max", C.c_int32), ("cluster", C.c_int32), ("block_threads", C.c_int32),
+                ("raster", C.c_int32)]
 
 
 class Keypoints(C.Structure):

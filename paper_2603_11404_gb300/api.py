@@ -16,6 +16,7 @@ from . import _abi
 from ._abi import call
 
 LOSS_XOR, LOSS_ONE_MINUS_IOU, LOSS_MSE_APP = 0, 1, 2
+RASTER_AUTO, RASTER_CLUSTER, RASTER_BINNED = 0, 1, 2
 
 
 # the current stream's handle in one call each (torch.cuda.current_stream()
@@ -53,7 +54,7 @@ class Tracker:
     """tracker_create(mesh, links, intrinsics) and the fitness entry points."""
 
     def __init__(self, scene, loss_kind: int = LOSS_XOR, lambda_max: int = 64, cull_backfaces: bool = False,
-                 lambda_app: float = 0.0, cluster: int = 0, block_threads: int = 0):
+                 lambda_app: float = 0.0, cluster: int = 0, block_threads: int = 0, raster: int = 0):
         self.scene = scene
         K = scene.K
         self._keep = []
@@ -80,7 +81,7 @@ class Tracker:
         Ki = _abi.Intrinsics(float(K.fx), float(K.fy), float(K.cx), float(K.cy), int(K.width), int(K.height),
                              float(K.z_near))
         cfg = _abi.Config(int(loss_kind), float(lambda_app), int(bool(cull_backfaces)), int(lambda_max),
-                          int(cluster), int(block_threads))
+                          int(cluster), int(block_threads), int(raster))
         h = C.c_void_p()
         call("tracker_create", meshes, len(scene.meshes), C.byref(ch), C.byref(Ki), C.byref(cfg), C.byref(h))
         self.h = h

@@ -38,6 +38,29 @@ struct CamDev {
     float2 fx_df, fy_df;
 };
 
+// Binned pipeline (binned.cu): the screen is cut into tiles of kTileW x kTileH
+// pixels (two mask words by 32 rows); each candidate's live triangles are
+// binned by tile, and a tile's bin is rasterised in work items of up to
+// kBinChunk entries.
+constexpr int kTileW = 64;
+constexpr int kTileH = 32;
+constexpr int kTileWords = kTileH * (kTileW / 32);
+constexpr int kBinChunk = 1024;   // records per raster work item (taken 32 at a time by the warps of a CTA)
+constexpr int kBinMaxTilesPerAxis = 256;  // tile ranges are packed in 8-bit fields
+
+// Scratch of the binned pipeline, sized when the tracker is created.
+struct BinDev {
+    float *frames;       // [lam][n_inst][n_frames][24] projective rows of every candidate (hi, lo)
+    int2 *pool;          // [lam][pool_cap][3] snapped vertices of the binned triangles, grouped by tile
+    int4 *items;         // [max_items] raster work items: candidate, tile | tx << 16 | ty << 24,
+                         // first pool record, records | chunks of the tile << 9
+    uint32_t *merge;     // [lam][n_tiles][kTileWords] OR of a multi-chunk tile (zero between launches)
+    int *tile_done;      // [lam][n_tiles] finished chunks of a multi-chunk tile (zero between launches)
+    int *acc;            // [lam][4] s, I, culled, unused (zeroed by the front kernel)
+    unsigned *ctl;       // [4] items, item ticket, exit ticket, m (zero between launches)
+    int n_tx, n_ty, n_tiles, pool_cap, max_items, live_cap, tiles_grid, pad[3];
+};
+
 // Everything one fitness launch needs (a multiple of 16 bytes: batched
 // launches copy it into shared memory in 16-byte pieces).
 struct __align__(16) EvalArgs {
@@ -73,6 +96,7 @@ struct __align__(16) EvalArgs {
     float kp_pt[2][3];
     float kp_tau, kp_lambda;
     const float *kp_obs;
+    BinDev bin;            // binned pipeline scratch (unused by the cluster-bitmap kernel)
 };
 
 struct LaunchCfg {
@@ -140,6 +164,15 @@ __host__ __device__ inline float2 split_df(double x)
 }
 
 cudaError_t launch_eval(const EvalArgs &a, const LaunchCfg &cfg, cudaStream_t s);
+// Binned pipeline: the front kernel (cluster of cfg.cluster CTAs per candidate)
+// and the persistent tile kernel; fused CMA-ES generations when a.cma_st is set.
+cudaError_t launch_binned(const EvalArgs &a, const LaunchCfg &cfg, cudaStream_t s);
+size_t binned_front_smem_bytes(const EvalArgs &a, int threads);
+size_t binned_tiles_smem_bytes();
+cudaError_t prepare_binned(size_t front_smem, int *tiles_per_sm);
+// Raise a kernel's dynamic shared memory limit on the current device to at
+// least smem (kept per device and kernel; thread-safe).
+cudaError_t ensure_smem_attr(const void *func, size_t smem);
 cudaError_t launch_project_keypoints(const EvalArgs &a, const float *states, int n, float *out, cudaStream_t s);
 size_t tell_smem_bytes();
 cudaError_t launch_eval_batch(const EvalArgs *descs_dev, const uint32_t *const *masks_dev, const int2 *items_dev,
@@ -187,6 +220,9 @@ struct trk_tracker {
     float4 *verts = nullptr;
     int4 *tris = nullptr;
     int2 *snap = nullptr;       // scratch [lambda_max * n_inst * V]
+    int raster = 0;             // TRK_RASTER_CLUSTER or TRK_RASTER_BINNED (resolved at create)
+    trk::BinDev bin{};          // binned pipeline scratch (raster == TRK_RASTER_BINNED)
+    trk::LaunchCfg lc_front{};  // launch shape of the binned front kernel
     uint32_t *zero_mask = nullptr;
     trk::LaunchCfg lc{};
     void *soft = nullptr;       // soft-silhouette scratch, allocated on first use

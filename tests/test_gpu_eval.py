@@ -30,11 +30,14 @@ def api():
     return a
 
 
+RASTERS = [1, 2]  # TRK_RASTER_CLUSTER, TRK_RASTER_BINNED
+
+
 def _check_population(api, scene, P, M, loss_kind=wl.LOSS_XOR, cull=False, lambda_max=None, lambda_app=0.0,
-                      cluster=0, threads=0, fk_tol=1e-4):
+                      cluster=0, threads=0, fk_tol=1e-4, raster=0):
     lam = P.shape[0]
     tr = api.Tracker(scene, loss_kind=loss_kind, lambda_max=lambda_max or max(lam, 1), cull_backfaces=cull,
-                     lambda_app=lambda_app, cluster=cluster, block_threads=threads)
+                     lambda_app=lambda_app, cluster=cluster, block_threads=threads, raster=raster)
     Md = torch.from_numpy(M).cuda()
     Mp = tr.pack_mask(Md)
     Pd = torch.from_numpy(np.ascontiguousarray(P, np.float32)).cuda()
@@ -82,14 +85,15 @@ def test_pack_mask_roundtrip(api):
     assert (pad == 0).all()  # bits past W are zero
 
 
+@pytest.mark.parametrize("raster", RASTERS)
 @pytest.mark.parametrize("rot", [wl.ROT_AXIS_ANGLE, wl.ROT_LOOKAT])
-def test_c1_population_parity(api, rot):
+def test_c1_population_parity(api, rot, raster):
     sc = wl.make_scene("c1", "c1", rot_param=rot)
     rng = np.random.default_rng(1000)
     gt = wl.sample_state(rng, sc.K, rot_param=rot)
     M = oracle.render(sc, gt)
     P = wl.population_around(rng, gt, 16)
-    counts, loss, _ = _check_population(api, sc, P, M, wl.LOSS_XOR)
+    counts, loss, _ = _check_population(api, sc, P, M, wl.LOSS_XOR, raster=raster)
     assert counts[:, 0].min() > 100  # the tool is in view
 
 
@@ -103,25 +107,29 @@ def test_loss_kinds_with_corrupted_mask(api, loss_kind):
     _check_population(api, sc, P, M, loss_kind, lambda_app=0.37)
 
 
-def test_c2_population_parity(api):
-    """640x512, ~20k triangles, lam = 64, 1 - IoU: the metric's configuration."""
+@pytest.mark.parametrize("raster", RASTERS)
+def test_c2_population_parity(api, raster):
+    """640x512, ~20k triangles, lam = 64, 1 - IoU: the metric's configuration
+    (the binned form draws its densest tiles in several work items and merges
+    them)."""
     sc = wl.make_scene("c2", "c2")
     rng = np.random.default_rng(2000)
     gt = wl.sample_state(rng, sc.K)
     M = wl.corrupt_mask(oracle.render(sc, gt), rng)
     P = wl.population_around(rng, gt, 64)
-    counts, loss, nd = _check_population(api, sc, P, M, wl.LOSS_ONE_MINUS_IOU)
+    counts, loss, nd = _check_population(api, sc, P, M, wl.LOSS_ONE_MINUS_IOU, raster=raster)
     assert nd <= 2
 
 
-def test_bimanual_and_ragged_image(api):
+@pytest.mark.parametrize("raster", RASTERS)
+def test_bimanual_and_ragged_image(api, raster):
     K = wl.Intrinsics(150.0, 150.0, 50.0, 38.5, 101, 77)
     sc = wl.make_scene("c1", "c1", n_instruments=2, K=K)
     rng = np.random.default_rng(5)
     gt = np.concatenate([wl.sample_state(rng, K), wl.sample_state(rng, K)])
     M = wl.corrupt_mask(oracle.render(sc, gt), rng)
     P = wl.population_around(rng, gt, 7)
-    _check_population(api, sc, P, M, wl.LOSS_ONE_MINUS_IOU, lambda_max=9)
+    _check_population(api, sc, P, M, wl.LOSS_ONE_MINUS_IOU, lambda_max=9, raster=raster)
 
 
 def test_branched_chain_matches_oracle(api):
@@ -143,40 +151,45 @@ def test_branched_chain_matches_oracle(api):
     _check_population(api, sc, P, M, wl.LOSS_ONE_MINUS_IOU)
 
 
-def test_largest_image(api):
-    """1280 x 1280, the largest image a tracker takes (a 200 KB bitmap per CTA),
-    with the 5000-triangle mesh close to the camera."""
+@pytest.mark.parametrize("raster", RASTERS)
+def test_largest_image(api, raster):
+    """1280 x 1280, the largest image a tracker takes (a 200 KB bitmap per CTA
+    in the cluster form, 20 x 40 tiles in the binned form), with the
+    5000-triangle mesh close to the camera."""
     K = wl.Intrinsics(1600.0, 1600.0, 640.0, 640.0, 1280, 1280)
     sc = wl.make_scene("5000", "c1", K=K)
     rng = np.random.default_rng(37)
     gt = wl.sample_state(rng, K, z_range=(60.0, 90.0))
     M = wl.corrupt_mask(oracle.render(sc, gt), rng)
     P = wl.population_around(rng, gt, 3)
-    counts, _, _ = _check_population(api, sc, P, M, wl.LOSS_ONE_MINUS_IOU)
+    counts, _, _ = _check_population(api, sc, P, M, wl.LOSS_ONE_MINUS_IOU, raster=raster)
     assert counts[:, 0].min() > 10000
 
 
-def test_single_candidate_and_cull_mode(api):
+@pytest.mark.parametrize("raster", RASTERS)
+def test_single_candidate_and_cull_mode(api, raster):
     sc = wl.make_scene("c1", "c1")
     rng = np.random.default_rng(6)
     gt = wl.sample_state(rng, sc.K)
     M = oracle.render(sc, gt)
     P = wl.population_around(rng, gt, 1)
-    _check_population(api, sc, P, M, cull=True)
+    _check_population(api, sc, P, M, cull=True, raster=raster)
 
 
+@pytest.mark.parametrize("raster", RASTERS)
 @pytest.mark.parametrize("cluster,threads", [(1, 32), (1, 64), (2, 128), (8, 256), (3, 96)])
-def test_launch_shapes_agree(api, cluster, threads):
+def test_launch_shapes_agree(api, cluster, threads, raster):
     sc = wl.make_scene("c1", "c1")
     rng = np.random.default_rng(7)
     gt = wl.sample_state(rng, sc.K)
     M = oracle.render(sc, gt)
     P = wl.population_around(rng, gt, 5)
-    _check_population(api, sc, P, M, cluster=cluster, threads=threads)
+    _check_population(api, sc, P, M, cluster=cluster, threads=threads, raster=raster)
 
 
+@pytest.mark.parametrize("raster", RASTERS)
 @pytest.mark.parametrize("cluster,threads", [(1, 64), (4, 64), (2, 96)])
-def test_bimanual_launch_shapes_agree(api, cluster, threads):
+def test_bimanual_launch_shapes_agree(api, cluster, threads, raster):
     """Two instruments with one or two warps beyond the composing ones (with
     64 threads every warp composes and also clears the bitmap)."""
     K = wl.Intrinsics(150.0, 150.0, 50.0, 38.5, 101, 77)
@@ -185,10 +198,11 @@ def test_bimanual_launch_shapes_agree(api, cluster, threads):
     gt = np.concatenate([wl.sample_state(rng, K), wl.sample_state(rng, K)])
     M = wl.corrupt_mask(oracle.render(sc, gt), rng)
     P = wl.population_around(rng, gt, 4)
-    _check_population(api, sc, P, M, wl.LOSS_ONE_MINUS_IOU, cluster=cluster, threads=threads)
+    _check_population(api, sc, P, M, wl.LOSS_ONE_MINUS_IOU, cluster=cluster, threads=threads, raster=raster)
 
 
-def test_large_triangles_warp_path(api):
+@pytest.mark.parametrize("raster", RASTERS)
+def test_large_triangles_warp_path(api, raster):
     """Near-camera close-up: triangles wider than 32 px go to the warp path."""
     sc = wl.make_scene("c1", "c1")
     rng = np.random.default_rng(8)
@@ -196,11 +210,12 @@ def test_large_triangles_warp_path(api):
     gt[3:6] = [0.0, 0.0, 25.0]
     M = random_mask(rng, sc.K.height, sc.K.width)
     P = wl.population_around(rng, gt, 6, sigma_mm=0.5)
-    counts, _, _ = _check_population(api, sc, P, M)
+    counts, _, _ = _check_population(api, sc, P, M, raster=raster)
     assert counts[:, 0].max() > 2000
 
 
-def test_full_screen_quad_and_overflow(api):
+@pytest.mark.parametrize("raster", RASTERS)
+def test_full_screen_quad_and_overflow(api, raster):
     """Two triangles covering all W*H pixel centres, plus many large triangles
     (more than the deferred-list capacity, so the CTA redraws every large
     triangle after its loop)."""
@@ -221,7 +236,7 @@ def test_full_screen_quad_and_overflow(api):
     sc = tiny_scene(W, H, fx, verts, tris)
     st = np.array([[0, 0, 0, 0, 0, z, 0, 0, 0]], np.float32)
     M = random_mask(rng, H, W)
-    counts, _, _ = _check_population(api, sc, st, M, cluster=1, threads=256)
+    counts, _, _ = _check_population(api, sc, st, M, cluster=1, threads=256, raster=raster)
     assert counts[0, 0] == W * H
 
 
@@ -245,6 +260,45 @@ def test_deferred_list_overflow_draws_every_large_triangle(api):
     M = random_mask(rng, H, W)
     counts, _, _ = _check_population(api, sc, st, M, cluster=1, threads=256)
     assert 0.2 * W * H < counts[0, 0] < 0.9 * W * H  # not saturated: every triangle matters
+
+
+def test_binned_pool_overflow_draws_tiles_from_every_triangle(api):
+    """A fan of 200 sectors (radius 650 px) of a disc in a 1024 x 1024 image:
+    each sector's box touches about 70 of the 512 tiles, 14k bin entries in
+    all, more than a candidate's pool holds (three per triangle + 8192), so
+    every tile is drawn from all triangles instead.  The fan is watertight
+    (fragments = union, checked on the oracle) and covers 85 % of the image,
+    so a sector left out or drawn twice would change the counts."""
+    W, H, fx, z = 1024, 1024, 100.0, 100.0
+    n, R = 200, 650.0
+    ax, ay = 300.0 - W / 2, 500.0 - H / 2
+    verts = [[ax * z / fx, ay * z / fx, 0.0]]
+    for t in np.linspace(0, 2 * np.pi, n + 1)[:-1]:
+        verts.append([(ax + R * np.cos(t)) * z / fx, (ay + R * np.sin(t)) * z / fx, 0.0])
+    tris = [[0, 1 + k, 1 + (k + 1) % n] for k in range(n)]
+    sc = tiny_scene(W, H, fx, verts, tris)
+    st = np.array([[0, 0, 0, 0, 0, z, 0, 0, 0], [0, 0, 0.02, 5.0, -3.0, z, 0, 0, 0]], np.float32)
+    rng = np.random.default_rng(41)
+    M = random_mask(rng, H, W)
+    for raster in RASTERS:
+        counts, _, _ = _check_population(api, sc, st, M, raster=raster)
+        assert 0.8 * W * H < counts[0, 0] < 0.9 * W * H
+
+
+def test_rasterisers_agree_on_tracking_workload(api):
+    """The two rasterisers give identical counts and losses on 640x512
+    populations of several trajectory frames (and so identical CMA-ES runs)."""
+    sc = wl.make_scene("c2", "c2")
+    rng = np.random.default_rng(2024)
+    gt0 = wl.sample_state(rng, sc.K)
+    traj = wl.sinusoidal_trajectory(rng, gt0, 4)
+    trs = [api.Tracker(sc, loss_kind=wl.LOSS_ONE_MINUS_IOU, lambda_max=64, raster=r) for r in RASTERS]
+    for f in range(4):
+        M = torch.from_numpy(wl.corrupt_mask(oracle.render(sc, traj[f]), rng)).cuda()
+        P = torch.from_numpy(wl.population_around(rng, traj[f], 64)).cuda()
+        out = [tr.eval_population(P, tr.pack_mask(M), counts=True) for tr in trs]
+        assert torch.equal(out[0][1], out[1][1])
+        assert torch.equal(out[0][0].view(torch.int32), out[1][0].view(torch.int32))
 
 
 def test_all_vertices_flagged_and_nan(api):
