@@ -31,6 +31,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_2603_11404_gb300 import metrics  # noqa: E402
 from paper_2603_11404_gb300 import workload as wl  # noqa: E402
 
 METRIC = "candidate pose evals/sec (render+loss) at 640x512, λ=64; p99 frame latency"
@@ -40,11 +41,11 @@ SEED = 2000
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 ALGO_OPS_PER_VERT, ALGO_OPS_PER_TRI, ALGO_OPS_PER_BBOX_PX = 16, 40, 4
 # DRAM bytes (read + write) of one plain k_eval launch at 640x512, lambda = 64, from
-# ncu (profiles/k_eval_640x512.md), valid for the kernel sources with this digest;
-# reported as null once those sources change.
+# the committed ncu capture of that kernel, valid for the kernel sources with this
+# digest; reported as null once those sources change.
 KEVAL_TRAFFIC_BYTES = 606976
 KEVAL_TRAFFIC_DIGEST = "6c589f918eb2d341"
-KERNEL_SOURCES = ("raster.cu", "cma_device.cuh", "df.cuh", "internal.cuh")
+KERNEL_SOURCES = ("raster.cu", "raster_dev.cuh", "cma_device.cuh", "df.cuh", "internal.cuh")
 
 
 def _kernel_digest():
@@ -65,7 +66,9 @@ def _args():
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-forms", action="store_true", help="skip the batching and serving measurements")
-    p.add_argument("--serve-frames", type=int, default=300, help="frames per camera stream in the serving run")
+    p.add_argument("--serve-frames", type=int, default=1000, help="frames per camera stream in the serving run")
+    p.add_argument("--long-frames", type=int, default=2500,
+                   help="frames of the longer run that reports the spread of the frame time")
     p.add_argument("--profile-target", action="store_true",
                    help="run a short fixed launch sequence for ncu (2 warm-up + 3 plain k_eval launches at "
                         "640x512, lambda = 64, then 3 fused generations, then 4 ask / fitness / update rounds) "
@@ -225,7 +228,21 @@ def run_ours(a):
         dist.barrier()
     evals = ws * a.steps * LAM * GENS
     value = job_throughput(ws, a.steps, LAM * GENS, total_s)
-    pose_err = np.abs(poses[a.warmup:].cpu().numpy() - traj[a.warmup:].astype(np.float32))
+    P_est = poses[a.warmup:].cpu().numpy()
+    tracking = metrics.summarise([metrics.pose_errors(P_est[i], traj[a.warmup + i]) for i in range(a.steps)])
+
+    # ---- spread of the frame time over a longer run (about a second of frames) ----
+    n_long = max(a.steps, int(a.long_frames))
+    es_l = api.CMAES(tr, LAM, init, scales, sigma0=1.0, seed=SEED + rank + 31)
+    ev_l = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_long)]
+    pl = torch.empty(9, dtype=torch.float32, device="cuda")
+    for i in range(n_long):
+        f = i % n_frames
+        ev_l[i][0].record(stream)
+        es_l.track_frame(packed[f], GENS, pose_out=pl)
+        ev_l[i][1].record(stream)
+    torch.cuda.synchronize()
+    long_ms = np.array([s_.elapsed_time(e_) for s_, e_ in ev_l])
 
     # ---- e2e: the public host call (mask H2D from pinned memory, pose D2H) ----
     es2 = api.CMAES(tr, LAM, init, scales, sigma0=1.0, seed=SEED + rank)
@@ -297,9 +314,16 @@ def run_ours(a):
         "plain_eval": {"evals_per_s": LAM * ws / (k_med_ms / 1e3), "median_us": k_med_ms * 1e3, "launches": R,
                        "what": "eval_population of one 64-candidate population per launch (fitness only, no "
                                "CMA-ES update), L2 flushed between launches, CUDA events, median"},
-        "tracking_error": {"rot_rad_median": float(np.median(pose_err[:, :3])),
-                           "trans_mm_median": float(np.median(pose_err[:, 3:6])),
-                           "joint_median": float(np.median(pose_err[:, 6:]))},
+        "tracking_error": tracking | {"metric": "Sec. IV-B: geodesic rotation angle, translation distance, "
+                                                "joint-angle error; mean, standard error and median over the "
+                                                "timed frames"},
+        "frame_time_spread": {"frames": int(n_long), "ms_median": float(np.median(long_ms)),
+                              "ms_p10": float(np.percentile(long_ms, 10)),
+                              "ms_p90": float(np.percentile(long_ms, 90)),
+                              "ms_p99": float(np.percentile(long_ms, 99)),
+                              "evals_per_s_at_median": LAM * GENS / (float(np.median(long_ms)) / 1e3),
+                              "what": "tracked frames back to back (no L2 flush), device-resident masks "
+                                      "cycling through this run's frames, CUDA events per frame"},
         "clocks": clk.summary(),
     }
     if not a.no_forms:
@@ -448,10 +472,11 @@ def bench_soft(a, rank, tr, sc, traj, init, packed, flush, n_frames: int = 60, r
             ev.append((e0, e1))
         torch.cuda.synchronize()
         ms = np.array([x.elapsed_time(y) for x, y in ev])
-        err = np.abs(poses.cpu().numpy() - traj[:n].astype(np.float32))[5:]
+        P_est = poses.cpu().numpy()
+        err = metrics.summarise([metrics.pose_errors(P_est[f], traj[f]) for f in range(5, n)])
         return {"frame_ms_p50": float(np.median(ms)), "frame_ms_p99": float(np.percentile(ms, 99)),
-                "rot_rad_median": float(np.median(err[:, :3])), "trans_mm_median": float(np.median(err[:, 3:6])),
-                "joint_median": float(np.median(err[:, 6:]))}
+                "rot_rad_median": err["rot_rad"]["median"], "trans_mm_median": err["trans_mm"]["median"],
+                "joint_rad_median": err["joint_rad"]["median"], "errors": err}
 
     return {"workload": "640x512, %d-triangle mesh, sigma 1 px, cutoff 14 sigma, lambda=%d; tracking over %d frames "
                         "(errors after frame 5)" % (sc.n_tris, LAM, n),
@@ -546,7 +571,13 @@ def bench_batching(a, rank, n_frames: int = 6):
 
 
 SERVE_STREAMS = 8
-SERVE_CYCLE = 30  # distinct frames per stream; longer runs replay them in order
+SERVE_CYCLE = 30  # distinct frames per stream; longer runs play them forward and back (continuous motion)
+
+
+def _pingpong(f: int, n: int) -> int:
+    """Frame f of a sequence of n frames played forward, backward, forward, ..."""
+    p = f % (2 * n - 2) if n > 1 else 0
+    return p if p < n else 2 * n - 2 - p
 
 
 def bench_serving(a, rank):
@@ -586,7 +617,8 @@ def bench_serving(a, rank):
 
     def frame(k, f):
         x = streams[k]
-        return x["masks"][f % SERVE_CYCLE], (x["joints"][f % SERVE_CYCLE] if x["bim"] else None)
+        i = _pingpong(f, SERVE_CYCLE)
+        return x["masks"][i], (x["joints"][i] if x["bim"] else None)
 
     def served(realtime: bool):
         srv = api.Server(max_active=SERVE_STREAMS, max_streams=SERVE_STREAMS, max_pending=64,
@@ -598,13 +630,16 @@ def bench_serving(a, rank):
             srv.submit(sids[k], m, j, tag=1 << 40)
         srv.run_until_idle()
         res, i = [], 0
-        t0 = api.Server.now() + 0.05
+        # real time: frames arrive on the Poisson schedule; saturated: every
+        # frame arrives at t0 (submitted as fast as the staging pool allows,
+        # each stamped with t0, so latency includes the wait for the pool)
+        t0 = api.Server.now() + (0.05 if realtime else 0.0)
         while len(res) < len(arrivals):
             now = api.Server.now()
             while i < len(arrivals) and (not realtime or t0 + arrivals[i][0] <= now):
                 t, k, f = arrivals[i]
                 m, j = frame(k, f)
-                if not srv.submit(sids[k], m, j, tag=f, t_submit=(t0 + t) if realtime else -1.0):
+                if not srv.submit(sids[k], m, j, tag=f, t_submit=(t0 + t) if realtime else t0):
                     break  # staging pool full: step first (a real-time frame keeps its arrival time)
                 i += 1
             act, q = srv.step()
@@ -626,13 +661,15 @@ def bench_serving(a, rank):
             m, j = frame(k, 0)
             o.track_frame_host(m, GENS, j)
         lat = []
-        t0 = time.perf_counter() + 0.05
+        # the same arrival semantics as the served form: real time on the
+        # Poisson schedule, saturated with every frame arriving at t0
+        t0 = time.perf_counter() + (0.05 if realtime else 0.0)
         first = None
         for t, k, f in arrivals:
             if realtime:
                 while time.perf_counter() < t0 + t:
                     time.sleep(max(0.0, min(0.001, t0 + t - time.perf_counter())))
-            arr = t0 + t if realtime else time.perf_counter()
+            arr = t0 + t if realtime else t0
             first = arr if first is None else first
             m, j = frame(k, f)
             opts[k].track_frame_host(m, GENS, j)
@@ -644,11 +681,13 @@ def bench_serving(a, rank):
 
     return {"workload": "%d streams (4 joint-free d=9, 4 bi-manual d=18 with joint readings), 640x512, "
                         "20k-triangle meshes, lambda=64, %d generations, Poisson 30 Hz per stream, %d frames "
-                        "per stream (masks cycle through %d frames)" % (SERVE_STREAMS, GENS, n_per, SERVE_CYCLE),
+                        "per stream (a %d-frame trajectory played forward and back)" % (SERVE_STREAMS, GENS, n_per,
+                                                                                        SERVE_CYCLE),
             "served_realtime": served(True), "plain_realtime": plain(True),
             "served_saturated": served(False), "plain_saturated": plain(False),
             "latency": "t_done - arrival; t_done = device completion of the frame's last tick (pose download "
-                       "included) for the server, host return of track_frame_host for the plain form",
+                       "included) for the server, host return of track_frame_host for the plain form; saturated: "
+                       "every frame arrives at the start of the run in both forms",
             "results": "bit-identical poses alone, in the mix and in the plain form (tests/test_gpu_serve.py)"}
 
 
@@ -678,37 +717,33 @@ def _alu_peak():
 
 
 def cpu_baseline(seconds: float):
-    """The CPU oracle as it stands, on this host's cores, for a bounded sample."""
+    """The CPU oracle as it stands, on this host's cores, for a bounded sample:
+    only its eval_population is timed (populations and observed masks are
+    made before the timed loop)."""
     import oracle
     sc, traj, init = _workload(0, 64)
     cores = len(os.sched_getaffinity(0))
     rng = np.random.default_rng(99)
-    n, t0, f = 0, time.perf_counter(), 0
-    while True:
-        M = _corrupt(oracle.render(sc, traj[f % 64]), 0, f % 64)
-        P = wl.population_around(rng, traj[f % 64], LAM)
-        t1 = time.perf_counter()
-        oracle.eval_population(sc, P, M, n_threads=cores)
-        n += LAM
-        f += 1
-        if time.perf_counter() - t0 > seconds:
-            break
-    el = time.perf_counter() - t0
-    # the same oracle on one thread, a shorter bounded sample
-    n1, t1, g = 0, time.perf_counter(), 0
-    while True:
-        M = _corrupt(oracle.render(sc, traj[g % 64]), 0, g % 64)
-        P = wl.population_around(rng, traj[g % 64], LAM)
-        oracle.eval_population(sc, P, M, n_threads=1)
-        n1 += LAM
-        g += 1
-        if time.perf_counter() - t1 > max(1.0, seconds / 3):
-            break
-    el1 = time.perf_counter() - t1
-    return {"value": n / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{f} populations of {LAM} candidates (640x512, {sc.n_tris} triangles), "
-                      f"oracle renderer + counts over {cores} threads, {el:.1f} s incl. mask setup",
-            "value_1thread": n1 / el1, "sample_1thread": f"{g} populations on one thread, {el1:.1f} s",
+    n_prep = 16
+    masks = [_corrupt(oracle.render(sc, traj[f]), 0, f) for f in range(n_prep)]
+    pops = [wl.population_around(rng, traj[f], LAM) for f in range(n_prep)]
+
+    def timed(n_threads, budget):
+        n, f, el = 0, 0, 0.0
+        while el < budget:
+            t0 = time.perf_counter()
+            oracle.eval_population(sc, pops[f % n_prep], masks[f % n_prep], n_threads=n_threads)
+            el += time.perf_counter() - t0
+            n += LAM
+            f += 1
+        return n / el, f, el
+
+    v, f, el = timed(cores, seconds)
+    v1, g, el1 = timed(1, max(1.0, seconds / 3))  # the same oracle on one thread, a shorter sample
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{f} populations of {LAM} candidates (640x512, {sc.n_tris} triangles), oracle "
+                      f"eval_population over {cores} threads, {el:.1f} s of timed calls",
+            "value_1thread": v1, "sample_1thread": f"{g} populations on one thread, {el1:.1f} s",
             "cpu_model": _cpu_model()}
 
 
@@ -748,6 +783,7 @@ def run_reference(a):
     budget = 120.0
     t_start = time.perf_counter()
     done = 0
+    errs = []
     for f in range(n_frames):
         M = _corrupt(oracle.render(sc, traj[f]), 0, f)
         t0 = time.perf_counter()
@@ -755,6 +791,7 @@ def run_reference(a):
         if f >= a.warmup:
             times.append(time.perf_counter() - t0)
             done += 1
+            errs.append(metrics.pose_errors(est, traj[f]))
         if time.perf_counter() - t_start > budget and done >= 1:
             break
     total = sum(times)
@@ -767,7 +804,9 @@ def run_reference(a):
            "latency_ms": {"p50": float(np.percentile(times, 50) * 1e3), "p99": float(np.percentile(times, 99) * 1e3)},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                             "sample": f"{done} tracked frames x {GENS} generations x {LAM} candidates"},
-           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "tracking_error": metrics.summarise(errs) | {"metric": "Sec. IV-B, as in the GPU arm, on the same "
+                                                                  "trajectory and frames"}}
     print(json.dumps(out), flush=True)
 
 

@@ -51,10 +51,15 @@ typedef enum {
     TRK_EINVAL = 1,   /* rejected argument (nothing was enqueued)                 */
     TRK_ENOMEM = 2,   /* device or host allocation failed                          */
     TRK_ECUDA = 3,    /* a CUDA runtime call failed                                */
-    TRK_EDEVICE = 4,  /* a kernel raised the device error word                     */
-    TRK_ETIMEOUT = 5, /* a bounded device wait expired                             */
+    TRK_EDEVICE = 4,  /* a kernel raised an error bit of the device error word      */
     TRK_EBUSY = 6     /* admission refused (not enough free memory or slots)       */
-} trk_status;
+} trk_status;       /* (5 is unused: no kernel of this library waits on the device) */
+
+/* Bits of a tracker's device error word (tracker_get_error). */
+#define TRK_DEVERR_WORKLIST 0x1u    /* error: the binned rasteriser's work list overflowed
+                                       (an internal limit; the launch's counts are incomplete) */
+#define TRK_DEVERR_NONFINITE 0x8u   /* warning: a candidate's state held a NaN or an infinity
+                                       (its vertices were flagged, its triangles culled)  */
 
 #define TRK_MAX_FRAMES 16     /* kinematic frames per instrument                  */
 #define TRK_MAX_INSTRUMENTS 2 /* single arm or bi-manual (Sec. III-B)             */
@@ -145,6 +150,14 @@ trk_status tracker_create(const trk_link_mesh *meshes, int32_t n_meshes, const t
                           const trk_intrinsics *K, const trk_config *cfg, trk_tracker **out);
 trk_status tracker_destroy(trk_tracker *t);
 
+/* The tracker's device error word: every kernel launched for this tracker
+ * (fitness, fused generations, batches, servers) ORs TRK_DEVERR_* bits into
+ * it instead of trapping.  Synchronises `stream`, copies the word to
+ * *device_code (may be NULL) and clears it.  Returns TRK_EDEVICE if an error
+ * bit was set, else TRK_OK (warning bits alone still return TRK_OK).  Not a
+ * paper feature: the boundary's error reporting. */
+trk_status tracker_get_error(trk_tracker *t, uint32_t *device_code, void *stream);
+
 /* Sizes the tracker was created with (any pointer may be NULL). */
 trk_status tracker_info(const trk_tracker *t, int32_t *d, int32_t *n_verts, int32_t *n_tris,
                         int32_t *width, int32_t *height, int32_t *words_per_row);
@@ -198,15 +211,20 @@ trk_status eval_population_debug(trk_tracker *t, const float *params_dev, int32_
  * held by every GPU that loads the library until the process exits.
  *   verts_dev [n_verts*4] FP32: x, y, z (mm) and the vertex's frame index
  *     stored as a float; tris_dev [n_tris*4] int32: three vertex indices and
- *     one unused word.  Indices are NOT checked (they are in device memory):
- *     they must lie in [0, n_verts) and frames in [0, n_frames).
+ *     one unused word.  The host cannot validate device memory, so the kernel
+ *     checks them: a vertex whose frame is not an integer in [0, n_frames) is
+ *     treated as flagged, and a triangle with an index outside [0, n_verts)
+ *     is not drawn; both count as culled (counts_dev[4k+3]).
  *   chain, K, cfg: host structs as for tracker_create (cfg.lambda_max is
  *     ignored); params_dev, lam, mask_packed_dev, loss_dev, counts_dev: as
  *     for eval_population.
- * Errors: TRK_EINVAL (reason in tracker_last_error()) for bad arguments or
- * lam * n_instruments * n_verts > TRK_NOALLOC_MAX_SNAP; TRK_ECUDA.
- * The first call on each device looks up the scratch array's device address
- * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * Errors: TRK_EINVAL (reason in tracker_last_error()) for bad arguments (the
+ * host-side checks of tracker_create, lam > 65535, more than 2^24 vertices
+ * or triangles) or lam * n_instruments * n_verts > TRK_NOALLOC_MAX_SNAP;
+ * TRK_ECUDA.  Every call looks up the scratch array's device address on the
+ * current device (cudaGetSymbolAddress, which allocates nothing); the first
+ * call on a device also loads the library's kernels there, so make it before
+ * any stream capture.
  * Every call shares the array: calls whose kernels can overlap on the GPU
  * (other streams, other host threads) race on it and must be serialised by
  * the caller.  Asynchronous on `stream`. */
@@ -341,7 +359,9 @@ trk_status tracker_project_keypoints(trk_tracker *t, const float *states_dev, in
  *   S(p)   = 1 - prod_t (1 - a_t(p)) over every triangle of every link,
  *   L      = sum_p (S(p) - M(p))^2.
  * Triangles with a flagged vertex or zero area are left out.  FP32
- * throughout; sums use atomics, so the last bits may differ between runs.
+ * arithmetic; the loss sums the tiles' squared errors in a fixed order and
+ * the gradient sums are exact 64-bit fixed-point integers, so repeated calls
+ * give identical results.
  * ------------------------------------------------------------------------- */
 
 /* loss_dev[lam] = L of each candidate of params_dev [lam*d]; with grad_dev

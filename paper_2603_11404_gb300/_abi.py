@@ -18,8 +18,8 @@ TRK_MAX_D = 18
 TRK_MAX_LAMBDA = 1024
 TRK_MAX_PIXELS = 1280 * 1280
 
-STATUS = {0: "TRK_OK", 1: "TRK_EINVAL", 2: "TRK_ENOMEM", 3: "TRK_ECUDA", 4: "TRK_EDEVICE",
-          5: "TRK_ETIMEOUT", 6: "TRK_EBUSY"}
+STATUS = {0: "TRK_OK", 1: "TRK_EINVAL", 2: "TRK_ENOMEM", 3: "TRK_ECUDA", 4: "TRK_EDEVICE", 6: "TRK_EBUSY"}
+TRK_DEVERR_WORKLIST, TRK_DEVERR_NONFINITE = 0x1, 0x8
 
 
 class TrkError(RuntimeError):
@@ -76,6 +76,7 @@ SIGNATURES = {
     "tracker_create": [P, I32, P, P, P, P],
     "tracker_destroy": [P],
     "tracker_info": [P, P, P, P, P, P, P],
+    "tracker_get_error": [P, P, P],
     "tracker_pack_mask": [P, P, P, P],
     "eval_population": [P, P, I32, P, P, P, P],
     "eval_population_debug": [P, P, I32, P, P, P, P, P, P],

@@ -93,6 +93,13 @@ class Tracker:
         self.lambda_max = int(lambda_max)
         self.loss_kind = int(loss_kind)
 
+    def get_error(self, stream=None) -> int:
+        """tracker_get_error: the device error word's bits (TRK_DEVERR_*), cleared
+        by the read; raises TrkError (TRK_EDEVICE) when an error bit was set."""
+        w = C.c_uint32()
+        call("tracker_get_error", self.h, C.byref(w), _stream(stream))
+        return w.value
+
     def close(self):
         if getattr(self, "h", None):
             call("tracker_destroy", self.h)

@@ -53,7 +53,6 @@ const char *trk_status_string(trk_status s)
     case TRK_ENOMEM: return "out of memory";
     case TRK_ECUDA: return "CUDA error";
     case TRK_EDEVICE: return "device error";
-    case TRK_ETIMEOUT: return "device wait timed out";
     case TRK_EBUSY: return "busy";
     }
     return "unknown status";
@@ -80,6 +79,7 @@ static void tracker_free(trk_tracker *t)
     cudaFree(t->tris);
     cudaFree(t->snap);
     cudaFree(t->zero_mask);
+    cudaFree(t->err);
     binned_free(t->bin);
     soft_free(t);
     delete t;
@@ -271,14 +271,16 @@ trk_status tracker_create(const trk_link_mesh *meshes, int32_t n_meshes, const t
     if ((e = cudaMalloc(&t->verts, hv.size() * sizeof(float4))) != cudaSuccess ||
         (e = cudaMalloc(&t->tris, ht.size() * sizeof(int4))) != cudaSuccess ||
         (e = cudaMalloc(&t->snap, snap_elems * sizeof(int2))) != cudaSuccess ||
-        (e = cudaMalloc(&t->zero_mask, (size_t)cam.H * cam.Wq * 4)) != cudaSuccess) {
+        (e = cudaMalloc(&t->zero_mask, (size_t)cam.H * cam.Wq * 4)) != cudaSuccess ||
+        (e = cudaMalloc(&t->err, sizeof(unsigned))) != cudaSuccess) {
         tracker_free(t);
         g_last_error = std::string("cudaMalloc: ") + cudaGetErrorString(e);
         return e == cudaErrorMemoryAllocation ? TRK_ENOMEM : TRK_ECUDA;
     }
     if ((e = cudaMemcpy(t->verts, hv.data(), hv.size() * sizeof(float4), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(t->tris, ht.data(), ht.size() * sizeof(int4), cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemset(t->zero_mask, 0, (size_t)cam.H * cam.Wq * 4)) != cudaSuccess) {
+        (e = cudaMemset(t->zero_mask, 0, (size_t)cam.H * cam.Wq * 4)) != cudaSuccess ||
+        (e = cudaMemset(t->err, 0, sizeof(unsigned))) != cudaSuccess) {
         tracker_free(t);
         return cuda_fail(e, "tracker upload");
     }
@@ -368,6 +370,22 @@ trk_status tracker_destroy(trk_tracker *t)
 {
     if (!t) return inval("NULL tracker");
     tracker_free(t);
+    return TRK_OK;
+}
+
+trk_status tracker_get_error(trk_tracker *t, uint32_t *device_code, void *stream)
+{
+    if (!t) return inval("NULL tracker");
+    cudaStream_t s = as_stream(stream);
+    unsigned w = 0;
+    CU(cudaMemcpyAsync(&w, t->err, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "error word copy");
+    CU(cudaMemsetAsync(t->err, 0, sizeof(unsigned), s), "error word clear");
+    CU(cudaStreamSynchronize(s), "error word sync");
+    if (device_code) *device_code = w;
+    if (w & TRK_DEVERR_WORKLIST) {
+        g_last_error = "device error word: the binned rasteriser's work list overflowed";
+        return TRK_EDEVICE;
+    }
     return TRK_OK;
 }
 
@@ -610,6 +628,17 @@ trk_status cmaes_reset_device(trk_cmaes *es, const double *mean_dev, void *strea
 {
     if (!es || !mean_dev) return inval("NULL argument");
     CU(launch_cma_reset(es->k, es->st, mean_dev, false, nullptr, es->t->ch.n_inst, as_stream(stream)), "reset");
+    es->sqrt_pending = false;
+    return TRK_OK;
+}
+
+// Square roots left out by a frame's last generation, before work that needs
+// them (a reset makes them unnecessary).
+static trk_status ensure_sqrt(trk_cmaes *es, cudaStream_t s)
+{
+    if (!es->sqrt_pending) return TRK_OK;
+    CU(launch_cma_sqrt(es->k, es->st, s), "square roots");
+    es->sqrt_pending = false;
     return TRK_OK;
 }
 
@@ -625,6 +654,8 @@ trk_status cmaes_reset_host(trk_cmaes *es, const double *mean_host, void *stream
 static trk_status ask_impl(trk_cmaes *es, const double *z_in, float *params_dev, void *stream)
 {
     cudaStream_t s = as_stream(stream);
+    trk_status r = ensure_sqrt(es, s);
+    if (r != TRK_OK) return r;
     CU(launch_cma_ask(es->k, es->lam, es->st, es->y, es->z, es->params, z_in, s), "ask");
     if (params_dev && params_dev != es->params)
         CU(cudaMemcpyAsync(params_dev, es->params, sizeof(float) * es->lam * es->d, cudaMemcpyDeviceToDevice, s),
@@ -655,6 +686,8 @@ trk_status cmaes_last_normals(trk_cmaes *es, double *z_dev, void *stream)
 trk_status cmaes_tell(trk_cmaes *es, const float *loss_dev, void *stream)
 {
     if (!es || !loss_dev) return inval("NULL argument");
+    trk_status r = ensure_sqrt(es, as_stream(stream));
+    if (r != TRK_OK) return r;
     CU(launch_cma_tell(es->k, es->st, es->y, es->params, loss_dev, as_stream(stream)), "tell");
     return TRK_OK;
 }
@@ -665,6 +698,9 @@ trk_status cmaes_tell(trk_cmaes *es, const float *loss_dev, void *stream)
 static trk_status fused_generation(trk_cmaes *es, const uint32_t *mask, int finish, float *pose_out, void *stream)
 {
     trk_tracker *t = es->t;
+    trk_status r = ensure_sqrt(es, as_stream(stream));
+    if (r != TRK_OK) return r;
+    es->sqrt_pending = finish != 0;  // the finishing update leaves out the square roots
     EvalArgs a{};
     a.ch = t->ch;
     a.cam = t->cam;
@@ -742,6 +778,7 @@ trk_status track_frame_device(trk_cmaes *es, const uint32_t *mask_packed_dev, in
     if (generations < 1 || generations > 1000) return inval("generations out of range");
     cudaStream_t s = as_stream(stream);
     CU(launch_cma_reset(es->k, es->st, nullptr, true, joint_reading_dev, es->t->ch.n_inst, s), "frame reset");
+    es->sqrt_pending = false;
     for (int g = 0; g < generations; ++g) {
         trk_status r = fused_generation(es, mask_packed_dev, g == generations - 1, pose_out_dev, stream);
         if (r != TRK_OK) return r;
@@ -787,6 +824,8 @@ trk_status cmaes_save(trk_cmaes *es, void *blob, size_t *n, void *stream)
         return TRK_OK;
     }
     if (*n < need) return inval("blob too small");
+    trk_status r = ensure_sqrt(es, as_stream(stream));
+    if (r != TRK_OK) return r;
     BlobHeader h{kBlobMagic, 2u, (uint32_t)es->d, (uint32_t)es->lam, (uint32_t)sizeof(CmaState), 0u};
     memcpy(blob, &h, sizeof h);
     CU(cudaMemcpyAsync((char *)blob + sizeof h, es->st, sizeof(CmaState), cudaMemcpyDeviceToHost, as_stream(stream)),
@@ -808,6 +847,7 @@ trk_status cmaes_load(trk_cmaes *es, const void *blob, size_t n, void *stream)
     CU(cudaMemcpyAsync(es->st, (const char *)blob + sizeof h, sizeof(CmaState), cudaMemcpyHostToDevice,
                        as_stream(stream)),
        "load copy");
+    es->sqrt_pending = false;  // saved states carry their square roots
     CU(cudaStreamSynchronize(as_stream(stream)), "load sync");
     return TRK_OK;
 }

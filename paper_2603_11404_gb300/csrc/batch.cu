@@ -301,7 +301,8 @@ static cudaError_t enqueue_frame(trk_batch *b, int generations, cudaStream_t s)
         if ((e = launch_eval_batch(b->descs, b->masks, b->items, b->n_items, b->next_item, b->lc, b->n_clusters,
                                    s)) != cudaSuccess)
             break;
-        e = launch_cma_batch(1, b->n, nullptr, b->tb, s);
+        // the last generation's updates leave out the square roots (the next frame resets)
+        e = launch_cma_batch(g == generations - 1 ? 3 : 1, b->n, nullptr, b->tb, s);
     }
     if (e == cudaSuccess)
         e = launch_cma_batch(2, b->n, nullptr, b->tb, s);
@@ -313,6 +314,10 @@ trk_status batch_track_frame(trk_batch *b, const uint32_t *const *masks_dev, int
 {
     if (!b || !masks_dev || !poses_dev) return bfail(TRK_EINVAL, "NULL argument");
     if (!b->cma) return bfail(TRK_EINVAL, "batch was created without optimisers");
+    // every frame ends with updates that leave out the square roots: later
+    // single-optimiser work that samples without a reset runs them first
+    for (trk_cmaes *o : b->es)
+        if (o) o->sqrt_pending = true;
     if (generations < 1 || generations > 1000) return bfail(TRK_EINVAL, "generations out of range");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e;

@@ -162,6 +162,7 @@ __global__ void __launch_bounds__(256, 4) k_front(EvalArgs a)
         }
         if (warp < nI)
             compose_frames_warp(s_ch, a.cam, par + 9 * warp, sM + warp * nF * 24, scr + warp * kComposeScratch, lane);
+        if (rank == 0 && warp == nwarp - 1) check_state_finite(par, a.d, a.err, lane);
     }
     __syncthreads();
     if (rank == 0)
@@ -311,6 +312,7 @@ __global__ void __launch_bounds__(256, 4) k_front(EvalArgs a)
                                 : make_int4(c, tw, first + k * kBinChunk,
                                             min(kBinChunk, count - k * kBinChunk) | (n << 11));
             if (slot < a.bin.max_items) a.bin.items[slot] = it;
+            else if (a.err) atomicOr(a.err, TRK_DEVERR_WORKLIST);
         }
     }
     cluster.sync();  // no CTA reads another's counts any more (nor exits before they are read)
@@ -582,7 +584,7 @@ static __device__ __noinline__ void tiles_epilogue(const EvalArgs &a, unsigned c
     __syncthreads();
     if (a.cma_st) {
         TellSmem &S = *reinterpret_cast<TellSmem *>(smem);
-        cma_tell_block(*a.cma_k, a.cma_st, a.cma_y, a.params, a.loss, S, tid, nthr);
+        cma_tell_block(*a.cma_k, a.cma_st, a.cma_y, a.params, a.loss, S, tid, nthr, !a.cma_finish);
         __syncthreads();
         if (a.cma_finish) cma_finish_frame(*a.cma_k, a.cma_st, a.cma_pose_out, tid, nthr);
     }

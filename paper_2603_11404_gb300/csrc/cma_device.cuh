@@ -316,8 +316,25 @@ __device__ __forceinline__ void onesided_jacobi_regs(float *Xc, int lane, CmaSta
 // the index arithmetic below divides by d and by the number of Jacobi pairs,
 // which is cheap only for constant divisors.
 template <int DC>
+__device__ __forceinline__ void cma_sqrt_phases(const CmaConst &k, CmaState *st, TellSmem &S, int tid, int nt,
+                                                bool do_sigma, double sigma);
+
+// The step-size update (cumulative step-size adaptation) and the generation
+// counters, from |p_sigma|^2 in S.n2.
+__device__ __forceinline__ void cma_sigma_step(const CmaConst &k, CmaState *st, double n2, double sigma)
+{
+    double sg = sigma * exp(k.cs_over_ds * (sqrt(n2) * k.inv_chi - 1.0));
+    st->sigma = sg;
+    st->sigma_df = split_df(sg);
+    st->gen += 1;
+    st->gen_total += 1;
+}
+
+// do_sqrt = false leaves C^(1/2), C^(-1/2) and the eigenbasis as they were
+// (the caller either resets the search next or runs cma_sqrt_block first).
+template <int DC>
 __device__ __forceinline__ void cma_tell_impl(const CmaConst &k, CmaState *st, const double *y, const float *params,
-                                              const float *loss, TellSmem &S, int tid, int nt)
+                                              const float *loss, TellSmem &S, int tid, int nt, bool do_sqrt)
 {
     const int d = DC ? DC : k.d, lam = k.lam, dd = d * d, mu = k.mu;
     for (int i = tid; i < lam; i += nt) {
@@ -443,6 +460,20 @@ __device__ __forceinline__ void cma_tell_impl(const CmaConst &k, CmaState *st, c
     }
 #undef YSEL
     __syncthreads();
+    if (!do_sqrt) {
+        if (tid == 0) cma_sigma_step(k, st, S.n2, sigma);
+        return;
+    }
+    cma_sqrt_phases<DC>(k, st, S, tid, nt, true, sigma);
+}
+
+// C^(1/2), C^(-1/2) and the eigenbasis of C (S.C holds C, S.B the previous
+// basis), with the step-size update on the second warp when do_sigma.
+template <int DC>
+__device__ __forceinline__ void cma_sqrt_phases(const CmaConst &k, CmaState *st, TellSmem &S, int tid, int nt,
+                                                bool do_sigma, double sigma)
+{
+    const int d = DC ? DC : k.d, dd = d * d;
 
     // ---- eigendecomposition, phase 1: one-sided (Hestenes) Jacobi in FP32 on
     //      the columns of X = C B (B = last generation's basis, a warm start),
@@ -471,14 +502,8 @@ __device__ __forceinline__ void cma_tell_impl(const CmaConst &k, CmaState *st, c
         else
             onesided_jacobi_smem<DC>(S.Af, S.Vf2, d, tid, st);
     }
-    if (tid == (nt > 32 ? 32 : 0)) {
-        // step size (CSA): on the second warp, off the eigendecomposition's critical path
-        double sg = sigma * exp(k.cs_over_ds * (sqrt(S.n2) * k.inv_chi - 1.0));
-        st->sigma = sg;
-        st->sigma_df = split_df(sg);
-        st->gen += 1;
-        st->gen_total += 1;
-    }
+    if (do_sigma && tid == (nt > 32 ? 32 : 0))  // step size (CSA): on the second warp, off the eigendecomposition's critical path
+        cma_sigma_step(k, st, S.n2, sigma);
     __syncthreads();
     // ---- phase 2: V = orth(B J) in FP64 (two Newton-Schulz polar steps,
     //      V <- V (3 I - V^T V) / 2, taking 1e-6 to FP64 rounding); B J is the
@@ -618,11 +643,32 @@ __device__ __forceinline__ void cma_tell_impl(const CmaConst &k, CmaState *st, c
 
 static __device__ __noinline__ void cma_tell_block(const CmaConst &k, CmaState *st, const double *y,
                                                    const float *params, const float *loss, TellSmem &S, int tid,
-                                                   int nt)
+                                                   int nt, bool do_sqrt = true)
 {
-    if (k.d == 9) cma_tell_impl<9>(k, st, y, params, loss, S, tid, nt);
-    else if (k.d == 18) cma_tell_impl<18>(k, st, y, params, loss, S, tid, nt);
-    else cma_tell_impl<0>(k, st, y, params, loss, S, tid, nt);
+    if (k.d == 9) cma_tell_impl<9>(k, st, y, params, loss, S, tid, nt, do_sqrt);
+    else if (k.d == 18) cma_tell_impl<18>(k, st, y, params, loss, S, tid, nt, do_sqrt);
+    else cma_tell_impl<0>(k, st, y, params, loss, S, tid, nt, do_sqrt);
+}
+
+// The square roots and eigenbasis of the stored C alone: completes an update
+// made with do_sqrt = false (the step size was updated then).
+template <int DC>
+__device__ __forceinline__ void cma_sqrt_only(const CmaConst &k, CmaState *st, TellSmem &S, int tid, int nt)
+{
+    const int d = DC ? DC : k.d, dd = d * d;
+    for (int e = tid; e < dd; e += nt) {
+        S.C[e] = st->C[e];
+        S.B[e] = st->B[e];
+    }
+    __syncthreads();
+    cma_sqrt_phases<DC>(k, st, S, tid, nt, false, 0.0);
+}
+
+static __device__ __noinline__ void cma_sqrt_block(const CmaConst &k, CmaState *st, TellSmem &S, int tid, int nt)
+{
+    if (k.d == 9) cma_sqrt_only<9>(k, st, S, tid, nt);
+    else if (k.d == 18) cma_sqrt_only<18>(k, st, S, tid, nt);
+    else cma_sqrt_only<0>(k, st, S, tid, nt);
 }
 
 // Frame epilogue: the frame's best candidate becomes the estimate.

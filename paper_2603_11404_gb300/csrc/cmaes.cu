@@ -70,6 +70,14 @@ __global__ void __launch_bounds__(kTellThreads) k_cma_tell(const CmaConst *__res
     cma_tell_block(*kp, st, y, params, loss, S, threadIdx.x, blockDim.x);
 }
 
+// The square roots and eigenbasis of the stored covariance (after an update
+// that left them out).
+__global__ void __launch_bounds__(kTellThreads) k_cma_sqrt(const CmaConst *__restrict__ kp, CmaState *st)
+{
+    __shared__ TellSmem S;
+    cma_sqrt_block(*kp, st, S, threadIdx.x, blockDim.x);
+}
+
 __global__ void k_cma_finish(const CmaConst *__restrict__ kp, CmaState *st, float *pose_out)
 {
     cma_finish_frame(*kp, st, pose_out, threadIdx.x, blockDim.x);
@@ -89,11 +97,11 @@ __global__ void k_cma_reset_batch(const int *sel, const CmaConst *const *kp, Cma
 __global__ void __launch_bounds__(kTellThreads) k_cma_tell_batch(const int *sel, const CmaConst *const *kp,
                                                                  CmaState *const *st, const double *const *y,
                                                                  const float *const *params,
-                                                                 const float *const *loss)
+                                                                 const float *const *loss, int do_sqrt)
 {
     __shared__ TellSmem S;
     const int i = batch_instance(sel);
-    cma_tell_block(*kp[i], st[i], y[i], params[i], loss[i], S, threadIdx.x, blockDim.x);
+    cma_tell_block(*kp[i], st[i], y[i], params[i], loss[i], S, threadIdx.x, blockDim.x, do_sqrt != 0);
 }
 
 __global__ void k_cma_finish_batch(const int *sel, const CmaConst *const *kp, CmaState *const *st,
@@ -107,7 +115,7 @@ cudaError_t launch_cma_batch(int op, int n, const int *sel, const BatchTables &t
 {
     if (n == 0) return cudaSuccess;
     if (op == 0) k_cma_reset_batch<<<n, 128, 0, s>>>(sel, t.k, t.st, t.ninst, t.joint);
-    if (op == 1) k_cma_tell_batch<<<n, kTellThreads, 0, s>>>(sel, t.k, t.st, t.y, t.params, t.loss);
+    if (op == 1 || op == 3) k_cma_tell_batch<<<n, kTellThreads, 0, s>>>(sel, t.k, t.st, t.y, t.params, t.loss, op == 1);
     if (op == 2) k_cma_finish_batch<<<n, 32, 0, s>>>(sel, t.k, t.st, t.pose);
     return cudaGetLastError();
 }
@@ -130,6 +138,12 @@ cudaError_t launch_cma_tell(const CmaConst *k, CmaState *st, const double *y, co
                             const float *loss, cudaStream_t s)
 {
     k_cma_tell<<<1, kTellThreads, 0, s>>>(k, st, y, params, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cma_sqrt(const CmaConst *k, CmaState *st, cudaStream_t s)
+{
+    k_cma_sqrt<<<1, kTellThreads, 0, s>>>(k, st);
     return cudaGetLastError();
 }
 

@@ -97,6 +97,8 @@ struct __align__(16) EvalArgs {
     float kp_tau, kp_lambda;
     const float *kp_obs;
     BinDev bin;            // binned pipeline scratch (unused by the cluster-bitmap kernel)
+    unsigned *err;         // the tracker's device error word (TRK_DEVERR_*), or NULL
+    int pad_err[2];
 };
 
 struct LaunchCfg {
@@ -164,6 +166,10 @@ __host__ __device__ inline float2 split_df(double x)
 }
 
 cudaError_t launch_eval(const EvalArgs &a, const LaunchCfg &cfg, cudaStream_t s);
+// The cluster-bitmap kernel with index checks (meshes in the caller's device
+// memory): a vertex whose frame index is out of range is flagged, a triangle
+// with a vertex index out of range is culled.
+cudaError_t launch_eval_checked(const EvalArgs &a, const LaunchCfg &cfg, cudaStream_t s);
 // Binned pipeline: the front kernel (cluster of cfg.cluster CTAs per candidate)
 // and the persistent tile kernel; fused CMA-ES generations when a.cma_st is set.
 cudaError_t launch_binned(const EvalArgs &a, const LaunchCfg &cfg, cudaStream_t s);
@@ -192,6 +198,9 @@ cudaError_t launch_cma_ask(const CmaConst *k, int lam, CmaState *st, double *y, 
 cudaError_t launch_cma_tell(const CmaConst *k, CmaState *st, const double *y, const float *params,
                             const float *loss, cudaStream_t s);
 cudaError_t launch_cma_finish_frame(const CmaConst *k, CmaState *st, float *pose_out, cudaStream_t s);
+// C^(1/2), C^(-1/2) and the eigenbasis of the stored C (completes an update
+// made without them).
+cudaError_t launch_cma_sqrt(const CmaConst *k, CmaState *st, cudaStream_t s);
 // Device tables (one entry per instance) for the batched CMA-ES kernels.
 struct BatchTables {
     const CmaConst **k = nullptr;
@@ -202,8 +211,9 @@ struct BatchTables {
     float **pose = nullptr;          // frame estimates written by the epilogue
     int *ninst = nullptr;
 };
-// op 0 reset from the estimate, 1 update, 2 frame epilogue; one block per
-// selected instance (sel[n] device indices, or NULL for instances 0..n-1)
+// op 0 reset from the estimate, 1 update, 2 frame epilogue, 3 update without
+// the square roots (a frame's last generation); one block per selected
+// instance (sel[n] device indices, or NULL for instances 0..n-1)
 cudaError_t launch_cma_batch(int op, int n, const int *sel, const BatchTables &t, cudaStream_t s);
 
 static_assert(sizeof(EvalArgs) % 16 == 0, "batched launches copy EvalArgs in 16-byte pieces");
@@ -224,6 +234,7 @@ struct trk_tracker {
     trk::BinDev bin{};          // binned pipeline scratch (raster == TRK_RASTER_BINNED)
     trk::LaunchCfg lc_front{};  // launch shape of the binned front kernel
     uint32_t *zero_mask = nullptr;
+    unsigned *err = nullptr;    // device error word (TRK_DEVERR_* bits)
     trk::LaunchCfg lc{};
     void *soft = nullptr;       // soft-silhouette scratch, allocated on first use
     // keypoint term (tracker_set_keypoints / tracker_set_keypoint_obs)
@@ -236,6 +247,7 @@ struct trk_tracker {
 // The tracker's keypoint term into a launch's arguments.
 inline void apply_keypoints(trk::EvalArgs &a, const trk_tracker *t)
 {
+    a.err = t->err;
     for (int k = 0; k < 2; ++k) {
         a.kp_frame[k] = t->kp_frame[k];
         for (int j = 0; j < 3; ++j) a.kp_pt[k][j] = t->kp_pt[k][j];
@@ -262,6 +274,9 @@ struct trk_cmaes {
     unsigned *done = nullptr;   // CTA ticket counter of the fused generation kernel
     void *refine = nullptr;     // gradient-refinement buffers, allocated on first use
     int lam = 0, d = 0;
+    // the last update left out the square roots (a frame's last generation):
+    // work that samples or updates again without a reset runs them first
+    bool sqrt_pending = false;
 };
 
 namespace trk {

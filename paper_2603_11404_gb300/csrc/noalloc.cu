@@ -13,7 +13,6 @@
 #include <string.h>
 
 #include <algorithm>
-#include <mutex>
 
 #include "internal.cuh"
 
@@ -26,34 +25,22 @@ namespace {
 // the GPU (different streams, or different host threads) race on it.
 static __device__ __align__(256) int2 g_noalloc_snap[TRK_NOALLOC_MAX_SNAP];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-int2 *g_snap_ptr[kMaxDevices];   // device address of g_noalloc_snap, per device
-bool g_snap_ready[kMaxDevices];
-
 trk_status fail(trk_status s, const char *why)
 {
     set_last_error(why);  // reported by tracker_last_error()
     return s;
 }
 
-// One-time set-up per device (with that device current): host code cannot
-// use the array's name as an address, so ask the runtime for it.
+// The array's device address on the current device.  Host code cannot use the
+// array's name as an address, so every call asks the runtime (a host-side
+// lookup that allocates nothing; looking it up each time keeps it right after
+// the device's context is reset or recreated).
 trk_status scratch_address(int2 **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_snap);
     if (e != cudaSuccess) return fail(TRK_ECUDA, cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices) return fail(TRK_EINVAL, "device index out of range");
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_snap_ready[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_snap);
-        if (e != cudaSuccess) return fail(TRK_ECUDA, cudaGetErrorString(e));
-        g_snap_ptr[dev] = static_cast<int2 *>(p);
-        g_snap_ready[dev] = true;
-    }
-    *out = g_snap_ptr[dev];
+    *out = static_cast<int2 *>(p);
     return TRK_OK;
 }
 
@@ -67,22 +54,31 @@ trk_status eval_population_noalloc(const float *verts_dev, int32_t n_verts, cons
                                    float *loss_dev, int32_t *counts_dev, void *stream)
 {
     if (!chain || !K || !cfg) return fail(TRK_EINVAL, "NULL chain, intrinsics or config");
-    if (lam < 0) return fail(TRK_EINVAL, "lam < 0");
+    if (lam < 0 || lam > 65535) return fail(TRK_EINVAL, "lam out of range (0..65535)");
     if (lam == 0) return TRK_OK;
     if (!verts_dev || !tris_dev || !params_dev || !mask_packed_dev || n_verts <= 0 || n_tris < 0)
         return fail(TRK_EINVAL, "NULL device pointer or empty mesh");
+    if (n_verts > (1 << 24) || n_tris > (1 << 24)) return fail(TRK_EINVAL, "mesh too large");
     if (chain->n_frames <= 0 || chain->n_frames > TRK_MAX_FRAMES) return fail(TRK_EINVAL, "n_frames out of range");
     if (chain->n_instruments < 1 || chain->n_instruments > TRK_MAX_INSTRUMENTS)
         return fail(TRK_EINVAL, "n_instruments must be 1 or 2");
     if (chain->rot_param != TRK_ROT_AXIS_ANGLE && chain->rot_param != TRK_ROT_LOOKAT)
         return fail(TRK_EINVAL, "rot_param");
-    for (int f = 0; f < chain->n_frames; ++f)
+    for (int f = 0; f < chain->n_frames; ++f) {
         if (chain->parent[f] >= f || chain->parent[f] < -1 || chain->axis[f] < 0 || chain->axis[f] > 3 ||
             chain->joint[f] < 0 || chain->joint[f] > 2)
             return fail(TRK_EINVAL, "chain frame fields");
+        for (int k = 0; k < 3; ++k)
+            if (!isfinite(chain->offset[f][k])) return fail(TRK_EINVAL, "offset not finite");
+        if (!isfinite(chain->coef[f])) return fail(TRK_EINVAL, "coef not finite");
+    }
+    for (int i = 0; i < 3; ++i)
+        if (!(chain->q_lb[i] <= chain->q_ub[i]) || !isfinite(chain->q_lb[i]) || !isfinite(chain->q_ub[i]))
+            return fail(TRK_EINVAL, "joint limits");
     if (K->width <= 0 || K->height <= 0 || (long long)K->width * K->height > TRK_MAX_PIXELS)
         return fail(TRK_EINVAL, "image size out of range");
-    if (!(K->fx > 0) || !(K->fy > 0) || !(K->z_near > 0)) return fail(TRK_EINVAL, "intrinsics");
+    if (!(K->fx > 0) || !(K->fy > 0) || !isfinite(K->fx) || !isfinite(K->fy)) return fail(TRK_EINVAL, "focal length");
+    if (!(K->z_near > 0) || !isfinite(K->z_near)) return fail(TRK_EINVAL, "z_near");
     const double cx256 = K->cx * 256.0, cy256 = K->cy * 256.0;
     if (cx256 != floor(cx256) || cy256 != floor(cy256) || fabs(cx256) > (1 << 22) || fabs(cy256) > (1 << 22))
         return fail(TRK_EINVAL, "256*cx and 256*cy must be integers");
@@ -117,7 +113,6 @@ trk_status eval_population_noalloc(const float *verts_dev, int32_t n_verts, cons
     }
     for (int i = 0; i < 3; ++i) {
         double range = chain->q_ub[i] - chain->q_lb[i];
-        if (!(range >= 0)) return fail(TRK_EINVAL, "joint limits");
         ch.q_lb[i] = chain->q_lb[i];
         ch.q_ub[i] = chain->q_ub[i];
         ch.lb_df[i] = split_df(chain->q_lb[i]);
@@ -162,9 +157,9 @@ trk_status eval_population_noalloc(const float *verts_dev, int32_t n_verts, cons
     }
     lc.smem = eval_smem_bytes(a);
     if (lc.smem > 227 * 1024) return fail(TRK_EINVAL, "image too large for the shared-memory bitmap");
-    cudaError_t e = prepare_eval(lc.smem);  // a kernel attribute, not an allocation
-    if (e != cudaSuccess) return fail(TRK_ECUDA, cudaGetErrorString(e));
-    e = launch_eval(a, lc, reinterpret_cast<cudaStream_t>(stream));
+    // the index-checked kernel: the mesh is in the caller's device memory; its
+    // dynamic shared-memory limit is a kernel attribute, not an allocation
+    cudaError_t e = launch_eval_checked(a, lc, reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return fail(TRK_ECUDA, cudaGetErrorString(e));
     return TRK_OK;
 }

@@ -71,7 +71,35 @@ cudaError_t launch_project_keypoints(const EvalArgs &a, const float *states, int
 // lets the last CTA of the launch run the CMA-ES update (single-instance mode).
 // Consecutive fused generations are launched with programmatic stream
 // serialisation (see griddep_wait).
-template <bool kInlineFallback>
+// Triangle t's vertex indices.  kChecked (meshes in the caller's device memory,
+// which the host cannot validate): an index outside [0, V) marks the triangle
+// bad (w = 1) and points it at vertex 0, so nothing outside the candidate's
+// vertices is read; gather3 then flags it, and it is culled.
+template <bool kChecked>
+__device__ __forceinline__ int4 load_tri(const EvalArgs &a, int t)
+{
+    const int b = t >= a.T;  // instrument (at most 2): no division
+    int4 tri = a.tris[t - b * a.T];
+    if (kChecked) {
+        const bool ok = (unsigned)tri.x < (unsigned)a.V && (unsigned)tri.y < (unsigned)a.V &&
+                        (unsigned)tri.z < (unsigned)a.V;
+        tri = ok ? make_int4(tri.x, tri.y, tri.z, 0) : make_int4(0, 0, 0, 1);
+    }
+    return tri;
+}
+
+// The three snapped vertices of a loaded triangle (written by other CTAs of
+// the cluster: read through L2).
+template <bool kChecked>
+__device__ __forceinline__ void gather3(const int2 *sv, int4 tri, int2 &v0, int2 &v1, int2 &v2)
+{
+    v0 = __ldcg(sv + tri.x);
+    v1 = __ldcg(sv + tri.y);
+    v2 = __ldcg(sv + tri.z);
+    if (kChecked && tri.w) v0.x = kSnapFlag;
+}
+
+template <bool kInlineFallback, bool kChecked = false>
 __device__ __forceinline__ void eval_candidate(const EvalArgs &a, int c, const uint32_t *mask_override,
                                                bool fused_tell, bool dependent_launch)
 {
@@ -123,6 +151,7 @@ __device__ __forceinline__ void eval_candidate(const EvalArgs &a, int c, const u
         if (warp < nI)
             compose_frames_warp(a.ch, a.cam, par + 9 * warp, sM + warp * nF * 24, scr + warp * kComposeScratch,
                                 lane);
+        if (rank == 0 && warp == nwarp - 1) check_state_finite(par, a.d, a.err, lane);
     }
     __syncthreads();
 
@@ -137,8 +166,20 @@ __device__ __forceinline__ void eval_candidate(const EvalArgs &a, int c, const u
         float4 p0 = a.verts[idx0 - b0 * a.V];
         float4 p1 = has1 ? a.verts[idx1 - b1 * a.V] : p0;
         float2 uv0, uv1;
-        int2 o0 = project_vertex(p0, sM + (b0 * nF + (int)p0.w) * 24, a.cam, uv0);
-        int2 o1 = project_vertex(p1, sM + (b1 * nF + (int)p1.w) * 24, a.cam, uv1);
+        int2 o0, o1;
+        const int f0 = (int)p0.w, f1 = (int)p1.w;
+        if (kChecked && !((unsigned)f0 < (unsigned)nF && (float)f0 == p0.w)) {  // a frame index out of range: flagged
+            o0 = make_int2(kSnapFlag, kSnapFlag);
+            uv0 = make_float2(0.0f, 0.0f);
+        } else {
+            o0 = project_vertex(p0, sM + (b0 * nF + f0) * 24, a.cam, uv0);
+        }
+        if (kChecked && !((unsigned)f1 < (unsigned)nF && (float)f1 == p1.w)) {
+            o1 = make_int2(kSnapFlag, kSnapFlag);
+            uv1 = make_float2(0.0f, 0.0f);
+        } else {
+            o1 = project_vertex(p1, sM + (b1 * nF + f1) * 24, a.cam, uv1);
+        }
         snapc[idx0] = o0;
         if (a.snap_dbg) a.snap_dbg[(size_t)c * NV + idx0] = o0;
         if (a.uv_dbg) a.uv_dbg[(size_t)c * NV + idx0] = uv0;
@@ -174,32 +215,22 @@ __device__ __forceinline__ void eval_candidate(const EvalArgs &a, int c, const u
         int2 v0 = make_int2(0, 0), v1 = v0, v2 = v0;
         if (t0 < NT) {
             const int b0 = t0 >= a.T;  // instrument (at most 2): no division
-            const int4 tri0 = a.tris[t0 - b0 * a.T];
-            const int2 *sv = snapc + b0 * a.V;
-            // written by other CTAs of the cluster in phase 1: read through L2
-            v0 = __ldcg(sv + tri0.x);
-            v1 = __ldcg(sv + tri0.y);
-            v2 = __ldcg(sv + tri0.z);
+            gather3<kChecked>(snapc + b0 * a.V, load_tri<kChecked>(a, t0), v0, v1, v2);
         }
         if (t1 < NT) {
             b1 = t1 >= a.T;
-            tri1 = a.tris[t1 - b1 * a.T];
+            tri1 = load_tri<kChecked>(a, t1);
         }
         while (cur * 32 < NT) {  // tickets of one warp increase: once past the end, done
             const int nx3 = ticket();
             int2 w0 = make_int2(0, 0), w1 = w0, w2 = w0;
-            if (t1 < NT) {
-                const int2 *svn = snapc + b1 * a.V;
-                w0 = __ldcg(svn + tri1.x);
-                w1 = __ldcg(svn + tri1.y);
-                w2 = __ldcg(svn + tri1.z);
-            }
+            if (t1 < NT) gather3<kChecked>(snapc + b1 * a.V, tri1, w0, w1, w2);
             const int t2 = nx2 * 32 + lane;
             int4 tri2 = make_int4(0, 0, 0, 0);
             int b2 = 0;
             if (t2 < NT) {
                 b2 = t2 >= a.T;
-                tri2 = a.tris[t2 - b2 * a.T];
+                tri2 = load_tri<kChecked>(a, t2);
             }
             if (t0 < NT) {
                 TriSetup t;
@@ -238,10 +269,10 @@ __device__ __forceinline__ void eval_candidate(const EvalArgs &a, int c, const u
     for (int e = warp; e < nbig; e += nwarp) {
         int tt = big[e];
         int b = tt >= a.T;
-        int4 tri = a.tris[tt - b * a.T];
-        const int2 *sv = snapc + b * a.V;
+        int2 u0, u1, u2;
+        gather3<kChecked>(snapc + b * a.V, load_tri<kChecked>(a, tt), u0, u1, u2);
         TriSetup t;
-        tri_setup(__ldcg(sv + tri.x), __ldcg(sv + tri.y), __ldcg(sv + tri.z), W, H, a.cull, t);
+        tri_setup(u0, u1, u2, W, H, a.cull, t);
         raster_warp(t, bm, Wq, lane);
     }
     if (!kInlineFallback && sacc[6]) {  // the list overflowed: every large triangle of the candidate, a warp each (drawing twice is harmless)
@@ -251,18 +282,17 @@ __device__ __forceinline__ void eval_candidate(const EvalArgs &a, int c, const u
             TriSetup t;
             if (tt < NT) {
                 const int b = tt >= a.T;
-                const int4 tri = a.tris[tt - b * a.T];
-                const int2 *sv = snapc + b * a.V;
-                large = tri_setup(__ldcg(sv + tri.x), __ldcg(sv + tri.y), __ldcg(sv + tri.z), W, H, a.cull, t) == 1 &&
-                        !(t.spanx < 32 * 256 && t.spany < 64 * 256);
+                int2 u0, u1, u2;
+                gather3<kChecked>(snapc + b * a.V, load_tri<kChecked>(a, tt), u0, u1, u2);
+                large = tri_setup(u0, u1, u2, W, H, a.cull, t) == 1 && !(t.spanx < 32 * 256 && t.spany < 64 * 256);
             }
             for (unsigned mm = __ballot_sync(0xffffffffu, large); mm; mm &= mm - 1) {
                 const int src = __ffs(mm) - 1, tu = __shfl_sync(0xffffffffu, tt, src);
                 const int b = tu >= a.T;
-                const int4 tri = a.tris[tu - b * a.T];
-                const int2 *sv = snapc + b * a.V;
+                int2 u0, u1, u2;
+                gather3<kChecked>(snapc + b * a.V, load_tri<kChecked>(a, tu), u0, u1, u2);
                 TriSetup u;
-                tri_setup(__ldcg(sv + tri.x), __ldcg(sv + tri.y), __ldcg(sv + tri.z), W, H, a.cull, u);
+                tri_setup(u0, u1, u2, W, H, a.cull, u);
                 raster_warp(u, bm, Wq, lane);
             }
         }
@@ -341,7 +371,9 @@ __device__ __forceinline__ void eval_candidate(const EvalArgs &a, int c, const u
         if (s_last) {
             __threadfence();
             TellSmem &S = *reinterpret_cast<TellSmem *>(smem);  // the cluster no longer reads this CTA's smem
-            cma_tell_block(*a.cma_k, a.cma_st, a.cma_y, a.params, a.loss, S, tid, nthr);
+            // a frame's last generation leaves out the square roots: the next
+            // frame restarts from C = I (the host runs them if it does not)
+            cma_tell_block(*a.cma_k, a.cma_st, a.cma_y, a.params, a.loss, S, tid, nthr, !a.cma_finish);
             __syncthreads();
             if (a.cma_finish) cma_finish_frame(*a.cma_k, a.cma_st, a.cma_pose_out, tid, nthr);
             if (tid == 0) *a.cma_done = 0u;
@@ -353,6 +385,13 @@ __global__ void __launch_bounds__(256, 4) k_eval(EvalArgs a)
 {
     griddep_launch_dependents();
     eval_candidate<false>(a, blockIdx.y, nullptr, true, true);
+}
+
+// The same with index checks: meshes in the caller's device memory
+// (eval_population_noalloc), whose indices the host cannot validate.
+__global__ void __launch_bounds__(256, 4) k_eval_checked(EvalArgs a)
+{
+    eval_candidate<false, true>(a, blockIdx.y, nullptr, false, false);
 }
 
 // Persistent batched evaluation: a fixed grid of clusters pulls (instance,
@@ -430,6 +469,26 @@ size_t eval_smem_bytes(const EvalArgs &a)
 int eval_max_threads() { return 1024; }
 
 cudaError_t prepare_eval(size_t smem) { return ensure_smem_attr((const void *)k_eval, smem); }
+
+cudaError_t launch_eval_checked(const EvalArgs &a, const LaunchCfg &cfg, cudaStream_t s)
+{
+    if (a.lam == 0) return cudaSuccess;
+    cudaError_t e = ensure_smem_attr((const void *)k_eval_checked, cfg.smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(cfg.cluster, a.lam, 1);
+    lc.blockDim = dim3(cfg.threads, 1, 1);
+    lc.dynamicSmemBytes = cfg.smem;
+    lc.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cfg.cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    return cudaLaunchKernelEx(&lc, k_eval_checked, a);
+}
 
 cudaError_t launch_eval(const EvalArgs &a, const LaunchCfg &cfg, cudaStream_t s)
 {

@@ -447,6 +447,14 @@ static __device__ float keypoint_loss(const EvalArgs &a, const float *sM)
     return a.kp_lambda * total;
 }
 
+// A candidate's state with a NaN or an infinity: its projection flags every
+// vertex; report it in the device error word (one warp per CTA calls this).
+__device__ __forceinline__ void check_state_finite(const float *st, int d, unsigned *err, int lane)
+{
+    const bool bad = lane < d && !isfinite(st[lane]);
+    if (__ballot_sync(0xffffffffu, bad) && lane == 0 && err) atomicOr(err, TRK_DEVERR_NONFINITE);
+}
+
 // Programmatic dependent launch: kernels that follow each other on a stream
 // are launched with programmatic stream serialisation, so the next kernel's
 // CTAs may be scheduled while this one is still running; they wait for this

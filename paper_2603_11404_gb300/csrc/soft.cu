@@ -41,6 +41,12 @@ constexpr float kSoftCutoff = 14.0f;   // in units of sigma
 constexpr int kTile = 16;              // tile edge (px): one pixel per thread
 constexpr int kSoftThreads = 256;
 constexpr int kChunk = 256;            // triangles staged per pass
+// Gradient sums are accumulated in 64-bit fixed point, exact and so independent
+// of the order of the (atomic) additions: dL/d(u, v) per vertex in units of
+// 2^-32 (|sum| < 2^31), the per-frame G_f in units of 2^-24 (|sum| < 2^39).
+constexpr double kGvScale = 4294967296.0;
+constexpr double kGScale = 16777216.0;
+__device__ __forceinline__ long long to_fixed(float x, double scale) { return __double2ll_rn((double)x * scale); }
 
 // ---------------------------------------------------------------------------
 // Forward-mode kinematics: every lane carries the values and one tangent
@@ -238,13 +244,13 @@ struct SoftArgs {
     const float *params;      // [lam * d]
     const uint32_t *mask;
     float4 *sv;               // [lam * nI * V]: u - cx, v - cy, Z, flag
-    float2 *gv;               // [lam * nI * V]: dL/du, dL/dv
+    longlong2 *gv;            // [lam * nI * V]: dL/du, dL/dv in fixed point (units of 2^-32)
     float *dT;                // [lam * nI * nF * 9 * 12]
     short4 *box;              // [lam * nI * T]: window j0, i0, j1, i1 (j0 > j1: none)
     int4 *cbox;               // [lam * nchunk]: union of the windows of each chunk
     int nchunk;
     int4 *ibox;               // [lam * nI]: window of the instrument
-    double *lacc;             // [lam]
+    double *lpart;            // [lam * ntx * nty]: squared error of each tile
     float *loss;              // [lam]
     float *grad;              // [lam * d] or NULL
 };
@@ -255,7 +261,6 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft_project(SoftArgs a)
     __shared__ float sT[kMaxFrames][12];
     __shared__ int bx[4];
     if (tid < 4) bx[tid] = (tid < 2) ? INT_MAX : INT_MIN;
-    if (b == 0 && tid == 0) a.lacc[c] = 0.0;
     if (tid < 32) {
         const int lane = tid, dir = lane - 1;
         float st[9];
@@ -295,7 +300,7 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft_project(SoftArgs a)
             }
         }
         a.sv[base + v] = make_float4(u, w, Z, flag);
-        a.gv[base + v] = make_float2(0.0f, 0.0f);
+        a.gv[base + v] = make_longlong2(0, 0);
     }
     atomicMin(&bx[0], j0);
     atomicMin(&bx[1], i0);
@@ -353,6 +358,7 @@ struct SoftTriSmem {
     short4 win[kChunk];
     int vid[3][kChunk];     // global vertex slots (into sv / gv)
     int list[kChunk];
+    int wc[kChunk / 32];    // staged triangles per warp (the compaction's prefix)
     int n;
 };
 
@@ -412,13 +418,13 @@ __device__ __forceinline__ float sigmoidf_(float x)
     return x >= 0.0f ? 1.0f / (1.0f + e) : e / (1.0f + e);
 }
 
-// Stage the triangles of chunk [t0, t0 + kChunk) whose window meets the tile.
+// Stage the triangles of chunk [t0, t0 + kChunk) whose window meets the tile,
+// in triangle order (a fixed order, so every sum over the staged triangles is
+// the same from run to run).
 __device__ void stage_chunk(const SoftArgs &a, int c, int t0, int tx0, int ty0, SoftTriSmem &S)
 {
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5;
     const int NT = a.nI * a.T;
-    if (tid == 0) S.n = 0;
-    __syncthreads();
     const int t = t0 + tid;
     bool hit = false;
     short4 w = make_short4(1, 1, 0, 0);
@@ -427,9 +433,15 @@ __device__ void stage_chunk(const SoftArgs &a, int c, int t0, int tx0, int ty0, 
         hit = w.x <= w.z && w.x <= tx0 + kTile - 1 && w.z >= tx0 && w.y <= ty0 + kTile - 1 && w.w >= ty0;
     }
     const unsigned bal = __ballot_sync(0xffffffffu, hit);
+    if ((tid & 31) == 0) S.wc[warp] = __popc(bal);
+    __syncthreads();
     int base = 0;
-    if ((tid & 31) == 0 && bal) base = atomicAdd(&S.n, __popc(bal));
-    base = __shfl_sync(0xffffffffu, base, 0);
+    for (int q = 0; q < warp; ++q) base += S.wc[q];
+    if (tid == 0) {
+        int n = 0;
+        for (int q = 0; q < kChunk / 32; ++q) n += S.wc[q];
+        S.n = n;
+    }
     if (hit) {
         const int slot = base + __popc(bal & ((1u << (tid & 31)) - 1u));
         const int b = t >= a.T;
@@ -514,10 +526,10 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft_tile(SoftArgs a)
     for (int o = 16; o; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
     if (lane == 0) red[warp] = l;
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0) {  // the tile's share, summed over the tiles in a fixed order by k_soft_reduce
         double sum = 0.0;
         for (int w = 0; w < 8; ++w) sum += (double)red[w];
-        atomicAdd(&a.lacc[c], sum);
+        a.lpart[(size_t)c * a.ntx * a.nty + tile] = sum;
     }
     if (!a.grad || !near) return;
     // pass 2: the same pairs again, one warp per staged triangle, lanes over
@@ -567,10 +579,10 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft_tile(SoftArgs a)
 #pragma unroll
             for (int q = 0; q < 6; ++q)
                 for (int o = 16; o; o >>= 1) g[q] += __shfl_xor_sync(0xffffffffu, g[q], o);
-            if (lane < 3) {
-                float *gp = reinterpret_cast<float *>(a.gv + S.vid[lane][e]);
-                atomicAdd(gp, g[2 * lane]);
-                atomicAdd(gp + 1, g[2 * lane + 1]);
+            if (lane < 3) {  // fixed point: the sums do not depend on the order of the additions
+                unsigned long long *gp = reinterpret_cast<unsigned long long *>(a.gv + S.vid[lane][e]);
+                atomicAdd(gp, (unsigned long long)to_fixed(g[2 * lane], kGvScale));
+                atomicAdd(gp + 1, (unsigned long long)to_fixed(g[2 * lane + 1], kGvScale));
             }
         }
         __syncthreads();
@@ -579,29 +591,45 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft_tile(SoftArgs a)
 
 // Per (candidate, instrument): dL/dX of every vertex, G_f = sum over the
 // frame's vertices of dL/dX [v; 1]^T, then dL/dtheta_k = sum_f <G_f, dT_f/dtheta_k>.
+// Block (c, 0) also sums the candidate's tile losses in a fixed order.  Every
+// sum is order-independent (fixed order, or exact fixed-point integers), so
+// a call's results do not vary from run to run.
 __global__ void __launch_bounds__(kSoftThreads) k_soft_reduce(SoftArgs a)
 {
     const int c = blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
-    __shared__ float G[kMaxFrames * 12];
-    if (b == 0 && tid == 0) a.loss[c] = (float)a.lacc[c];
+    __shared__ unsigned long long G[kMaxFrames * 12];  // fixed point, units of 2^-24
+    __shared__ double red[kSoftThreads];
+    if (b == 0) {
+        const int nt = a.ntx * a.nty;
+        double acc = 0.0;
+        for (int t = tid; t < nt; t += blockDim.x) acc += a.lpart[(size_t)c * nt + t];
+        red[tid] = acc;
+        __syncthreads();
+        for (int o = kSoftThreads / 2; o; o >>= 1) {
+            if (tid < o) red[tid] += red[tid + o];
+            __syncthreads();
+        }
+        if (tid == 0) a.loss[c] = (float)red[0];
+    }
     if (!a.grad) return;
-    for (int e = tid; e < a.nF * 12; e += blockDim.x) G[e] = 0.0f;
+    for (int e = tid; e < a.nF * 12; e += blockDim.x) G[e] = 0ull;
     __syncthreads();
     const size_t base = ((size_t)c * a.nI + b) * a.V;
     for (int v = tid; v < a.V; v += blockDim.x) {
         const float4 s = a.sv[base + v];
-        const float2 g = a.gv[base + v];
-        if (s.w != 0.0f || (g.x == 0.0f && g.y == 0.0f)) continue;
+        const longlong2 q = a.gv[base + v];
+        if (s.w != 0.0f || (q.x == 0 && q.y == 0)) continue;
+        const float gx = (float)((double)q.x * (1.0 / kGvScale)), gy = (float)((double)q.y * (1.0 / kGvScale));
         const float iz = 1.0f / s.z;
-        const float gX = g.x * a.fx * iz, gY = g.y * a.fy * iz, gZ = -(g.x * s.x + g.y * s.y) * iz;
+        const float gX = gx * a.fx * iz, gY = gy * a.fy * iz, gZ = -(gx * s.x + gy * s.y) * iz;
         const float4 p = a.verts[v];
-        float *Gf = G + (int)p.w * 12;
+        unsigned long long *Gf = G + (int)p.w * 12;
         const float vh[4] = {p.x, p.y, p.z, 1.0f};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            atomicAdd(Gf + k, gX * vh[k]);
-            atomicAdd(Gf + 4 + k, gY * vh[k]);
-            atomicAdd(Gf + 8 + k, gZ * vh[k]);
+            atomicAdd(Gf + k, (unsigned long long)to_fixed(gX * vh[k], kGScale));
+            atomicAdd(Gf + 4 + k, (unsigned long long)to_fixed(gY * vh[k], kGScale));
+            atomicAdd(Gf + 8 + k, (unsigned long long)to_fixed(gZ * vh[k], kGScale));
         }
     }
     __syncthreads();
@@ -609,7 +637,8 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft_reduce(SoftArgs a)
         float acc = 0.0f;
         for (int f = 0; f < a.nF; ++f) {
             const float *dT = a.dT + ((((size_t)c * a.nI + b) * a.nF + f) * 9 + tid) * 12;
-            for (int e = 0; e < 12; ++e) acc = fmaf(G[f * 12 + e], dT[e], acc);
+            for (int e = 0; e < 12; ++e)
+                acc = fmaf((float)((double)(long long)G[f * 12 + e] * (1.0 / kGScale)), dT[e], acc);
         }
         a.grad[(size_t)c * a.d + 9 * b + tid] = acc;
     }
@@ -697,12 +726,13 @@ namespace {
 struct SoftScratch {
     int cap = 0;
     float4 *sv = nullptr;
-    float2 *gv = nullptr;
+    longlong2 *gv = nullptr;
     float *dT = nullptr;
     short4 *box = nullptr;
     int4 *ibox = nullptr;
     int4 *cbox = nullptr;
-    double *lacc = nullptr;
+    double *lpart = nullptr;
+    int lpart_cap = 0;
 };
 
 struct RefineBuf {
@@ -730,17 +760,19 @@ trk_status soft_scratch(trk_tracker *t, int lam, SoftScratch **out)
     const size_t nv = (size_t)lam * nI * t->V;
     cudaError_t e;
     if ((e = cudaMalloc(&s->sv, sizeof(float4) * nv)) != cudaSuccess ||
-        (e = cudaMalloc(&s->gv, sizeof(float2) * nv)) != cudaSuccess ||
+        (e = cudaMalloc(&s->gv, sizeof(longlong2) * nv)) != cudaSuccess ||
         (e = cudaMalloc(&s->dT, sizeof(float) * (size_t)lam * nI * t->ch.n_frames * 9 * 12)) != cudaSuccess ||
         (e = cudaMalloc(&s->box, sizeof(short4) * (size_t)lam * nI * t->T)) != cudaSuccess ||
         (e = cudaMalloc(&s->ibox, sizeof(int4) * (size_t)lam * nI)) != cudaSuccess ||
         (e = cudaMalloc(&s->cbox, sizeof(int4) * (size_t)lam * ((nI * t->T + kChunk - 1) / kChunk))) != cudaSuccess ||
-        (e = cudaMalloc(&s->lacc, sizeof(double) * lam)) != cudaSuccess) {
+        (e = cudaMalloc(&s->lpart, sizeof(double) * lam * (size_t)((t->cam.W + kTile - 1) / kTile) *
+                                       ((t->cam.H + kTile - 1) / kTile))) != cudaSuccess) {
         t->soft = s;
         soft_free(t);
         return soft_fail(e == cudaErrorMemoryAllocation ? TRK_ENOMEM : TRK_ECUDA, cudaGetErrorString(e));
     }
     s->cap = lam;
+    s->lpart_cap = lam;
     t->soft = s;
     *out = s;
     return TRK_OK;
@@ -782,7 +814,7 @@ trk_status soft_launch(trk_tracker *t, const float *params, int lam, const uint3
     a.dT = s->dT;
     a.box = s->box;
     a.ibox = s->ibox;
-    a.lacc = s->lacc;
+    a.lpart = s->lpart;
     a.cbox = s->cbox;
     a.nchunk = (a.nI * a.T + kChunk - 1) / kChunk;
     a.loss = loss;
@@ -807,7 +839,7 @@ void trk::soft_free(trk_tracker *t)
     cudaFree(s->box);
     cudaFree(s->ibox);
     cudaFree(s->cbox);
-    cudaFree(s->lacc);
+    cudaFree(s->lpart);
     delete s;
     t->soft = nullptr;
 }

@@ -301,7 +301,9 @@ def test_rasterisers_agree_on_tracking_workload(api):
         assert torch.equal(out[0][0].view(torch.int32), out[1][0].view(torch.int32))
 
 
-def test_all_vertices_flagged_and_nan(api):
+@pytest.mark.parametrize("raster", RASTERS)
+def test_all_vertices_flagged_and_nan(api, raster):
+    from paper_2603_11404_gb300._abi import TRK_DEVERR_NONFINITE
     sc = wl.make_scene("c1", "c1")
     rng = np.random.default_rng(10)
     M = random_mask(rng, sc.K.height, sc.K.width)
@@ -309,13 +311,19 @@ def test_all_vertices_flagged_and_nan(api):
     P[0, 5] = -50.0          # behind the camera
     P[1, :] = np.nan         # non-finite state
     P[2, 3] = 1e6; P[2, 5] = 100.0  # far outside the guard band
-    tr = api.Tracker(sc, lambda_max=3)
+    tr = api.Tracker(sc, lambda_max=3, raster=raster)
     Mp = tr.pack_mask(torch.from_numpy(M).cuda())
+    assert tr.get_error() == 0
+    loss, counts = tr.eval_population(torch.from_numpy(P[[0, 2]]).cuda(), Mp, counts=True)
+    assert tr.get_error() == 0  # flagged vertices alone are no error
     loss, counts = tr.eval_population(torch.from_numpy(P).cuda(), Mp, counts=True)
     counts = counts.cpu().numpy()
     assert (counts[:, 0] == 0).all() and (counts[:, 1] == 0).all()
     assert (counts[:, 3] == sc.n_tris).all()
     assert (loss.cpu().numpy() == M.sum()).all()
+    # the NaN state is reported as a warning in the device error word, then cleared
+    assert tr.get_error() == TRK_DEVERR_NONFINITE
+    assert tr.get_error() == 0
 
 
 def test_empty_population_and_limits(api):

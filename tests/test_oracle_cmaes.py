@@ -41,6 +41,71 @@ def test_weights_and_constants():
         assert 0 < k["c_1"] + k["c_mu"] <= 1 and 0 < k["c_sigma"] < 1 and 0 < k["c_c"] <= 1
 
 
+# The learning rates at the two benchmark shapes, evaluated by hand from the
+# tutorial's default-parameter table (Hansen, arXiv:1604.00772, Table 1) to 30
+# digits and written here as literals.  lam = 64: mu = 32 and
+#   w'_i = ln(65/2) - ln i (i = 1..32),  mu_eff = (sum w')^2 / sum w'^2 = 17.621652406855657
+# (n-independent).  Then, for n = 9 and n = 18:
+#   c_sigma = (mu_eff + 2) / (n + mu_eff + 5)            = 0.6205131899622561 | 0.4830343239199235
+#   d_sigma = 1 + 2 max(0, sqrt((mu_eff-1)/(n+1)) - 1) + c_sigma
+#           (n = 9: sqrt(16.62/10) = 1.289, the max is 0.289; n = 18: sqrt(16.62/19) < 1, 0)
+#                                                        = 2.1990129403485661 | 1.4830343239199235
+#   c_c     = (4 + mu_eff/n) / (n + 4 + 2 mu_eff/n)      = 0.3522102497214471 | 0.2078215508657473
+#   c_1     = 2 / ((n + 1.3)^2 + mu_eff)                 = 0.0161666258682126 | 0.0051267374036655
+#   c_mu    = min(1 - c_1, 2 (mu_eff - 2 + 1/mu_eff) / ((n + 2)^2 + mu_eff))
+#                                                        = 0.2262042112722312 | 0.0750842332221743
+PINNED = {
+    (9, 64): dict(mu_eff=17.621652406855657, c_sigma=0.6205131899622561, d_sigma=2.1990129403485661,
+                  c_c=0.3522102497214471, c_1=0.0161666258682126, c_mu=0.2262042112722312),
+    (18, 64): dict(mu_eff=17.621652406855657, c_sigma=0.4830343239199235, d_sigma=1.4830343239199235,
+                   c_c=0.2078215508657473, c_1=0.0051267374036655, c_mu=0.0750842332221743),
+}
+
+
+def _pins_hold(k, n, lam):
+    """The constants k match the hand-evaluated values, and chi_n (the
+    tutorial's approximation of E|N(0, I)|) is within 2e-4 of the exact
+    sqrt(2) Gamma((n+1)/2) / Gamma(n/2)."""
+    from scipy.special import gammaln
+    want = PINNED[(n, lam)]
+    if any(abs(k[key] - v) > 1e-13 * abs(v) for key, v in want.items()):
+        return False
+    exact = math.sqrt(2.0) * math.exp(gammaln((n + 1) / 2.0) - gammaln(n / 2.0))
+    return abs(k["chi_n"] - exact) < 2e-4 * exact
+
+
+@pytest.mark.parametrize("n,lam", [(9, 64), (18, 64)])
+def test_learning_rates_pinned(n, lam):
+    assert _pins_hold(default_constants(n, lam), n, lam)
+
+
+def _planted(n, lam, which):
+    """default_constants with one plausible mistake planted (transposed or
+    dropped terms); the pins must reject every one of them."""
+    k = dict(default_constants(n, lam))
+    me = k["mu_eff"]
+    if which == "c_sigma":
+        k["c_sigma"] = (me + 2.0) / (n + me + 3.0)
+    elif which == "d_sigma":
+        k["d_sigma"] = 1.0 + 2.0 * max(0.0, math.sqrt((me - 1.0) / (n + 1.0)) - 1.0)
+    elif which == "c_c":
+        k["c_c"] = (4.0 + me / n) / (n + 4.0 + me / n)
+    elif which == "c_1":
+        k["c_1"] = 2.0 / ((n + 1.3) + me)
+    elif which == "c_mu":
+        k["c_mu"] = min(1.0 - k["c_1"], 2.0 * (me - 2.0 + 1.0 / me) / ((n + 1.0) ** 2 + me))
+    elif which == "chi_n":
+        k["chi_n"] = math.sqrt(n) * (1.0 - 1.0 / (4.0 * n) + 1.0 / (21.0 * n))
+    elif which == "mu_eff":
+        k["mu_eff"] = 1.0 / np.sum(k["w"] ** 3)
+    return k
+
+
+@pytest.mark.parametrize("which", ["c_sigma", "d_sigma", "c_c", "c_1", "c_mu", "chi_n", "mu_eff"])
+def test_learning_rate_pins_catch_planted_mistakes(which):
+    assert not all(_pins_hold(_planted(n, lam, which), n, lam) for n, lam in PINNED)
+
+
 def _run(f, d=9, lam=16, gens=200, seed=7, block=False, x0=None, sigma0=0.5):
     es = CMAES(d, lam, np.ones(d) if x0 is None else x0, np.ones(d), sigma0=sigma0, seed=seed,
                block_diag=block)
