@@ -43,8 +43,8 @@ ALGO_OPS_PER_VERT, ALGO_OPS_PER_TRI, ALGO_OPS_PER_BBOX_PX = 16, 40, 4
 # DRAM bytes (read + write) of one plain k_eval launch at 640x512, lambda = 64, from
 # the committed ncu capture of that kernel, valid for the kernel sources with this
 # digest; reported as null once those sources change.
-KEVAL_TRAFFIC_BYTES = 606976
-KEVAL_TRAFFIC_DIGEST = "6c589f918eb2d341"
+KEVAL_TRAFFIC_BYTES = 608000
+KEVAL_TRAFFIC_DIGEST = "5f34d76faa5ec78a"
 KERNEL_SOURCES = ("raster.cu", "raster_dev.cuh", "cma_device.cuh", "df.cuh", "internal.cuh")
 
 
@@ -69,10 +69,14 @@ def _args():
     p.add_argument("--serve-frames", type=int, default=1000, help="frames per camera stream in the serving run")
     p.add_argument("--long-frames", type=int, default=2500,
                    help="frames of the longer run that reports the spread of the frame time")
-    p.add_argument("--profile-target", action="store_true",
-                   help="run a short fixed launch sequence for ncu (2 warm-up + 3 plain k_eval launches at "
-                        "640x512, lambda = 64, then 3 fused generations, then 4 ask / fitness / update rounds) "
-                        "and exit")
+    p.add_argument("--profile-target", nargs="?", const="eval", default=None,
+                   choices=["eval", "binned", "soft", "batch", "serve", "pack"],
+                   help="run a short fixed launch sequence for ncu and exit: eval (default: 2 warm-up + 3 plain "
+                        "k_eval launches at 640x512, lambda = 64, then 3 fused generations, then 4 ask / fitness / "
+                        "update rounds), binned (5 evaluations by the binned rasteriser, same workload), soft (3 "
+                        "soft-silhouette forward + backward calls, 640x512, lambda = 16), batch (the 24-instance "
+                        "heterogeneous batch: autotune skipped, 3 tracked frames), serve (8 streams, 12 saturated "
+                        "frames each), pack (6 mask packings at 640x512)")
     return p.parse_args()
 
 
@@ -276,6 +280,18 @@ def run_ours(a):
     torch.cuda.synchronize()
     k_ms = np.array([s.elapsed_time(e) for s, e in kev])
     k_med_ms = max_over_ranks(float(np.median(k_ms)), ws, "cuda")
+    # the binned, tiled rasteriser on the same populations (the A/B of the two forms)
+    tr_b = api.Tracker(sc, loss_kind=wl.LOSS_ONE_MINUS_IOU, lambda_max=LAM, raster=api.RASTER_BINNED)
+    for i in range(3):
+        tr_b.eval_population(pops[i], packed[a.warmup + i], loss=loss_buf)
+    kevb = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(R)]
+    for i in range(R):
+        flush.fill_(i)
+        kevb[i][0].record(stream)
+        tr_b.eval_population(pops[i], packed[a.warmup + i], loss=loss_buf)
+        kevb[i][1].record(stream)
+    torch.cuda.synchronize()
+    kb_ms = np.array([s.elapsed_time(e) for s, e in kevb])
     # algorithmic work of those launches: 16 ops/vertex, 40 ops/live triangle,
     # 4 ops per pixel of each triangle's screen-clipped bounding box
     ops = 0.0
@@ -314,6 +330,10 @@ def run_ours(a):
         "plain_eval": {"evals_per_s": LAM * ws / (k_med_ms / 1e3), "median_us": k_med_ms * 1e3, "launches": R,
                        "what": "eval_population of one 64-candidate population per launch (fitness only, no "
                                "CMA-ES update), L2 flushed between launches, CUDA events, median"},
+        "raster_ab": {"cluster_bitmap_us_median": k_med_ms * 1e3, "binned_tiled_us_median": float(np.median(kb_ms)) * 1e3,
+                      "what": "the same populations through the two rasterisers (identical counts): one cluster per "
+                              "candidate with shared-memory full-image bitmaps (the default) against the binned, "
+                              "tiled pipeline (front kernel + persistent tile kernel)"},
         "tracking_error": tracking | {"metric": "Sec. IV-B: geodesic rotation angle, translation distance, "
                                                 "joint-angle error; mean, standard error and median over the "
                                                 "timed frames"},
@@ -455,6 +475,27 @@ def bench_soft(a, rank, tr, sc, traj, init, packed, flush, n_frames: int = 60, r
     fwd_ms = timed(lambda: tr.soft_eval(P, Mp))
     bwd_ms = timed(lambda: tr.soft_eval(P, Mp, grad=True))
     hard_ms = timed(lambda: tr.eval_population(P, Mp))
+    # roofline of the soft form: the tile kernel evaluates every (pixel,
+    # triangle) pair inside the triangle's window of influence (its pixel box
+    # grown by 14 sigma, clipped to the image): about 60 FP32 operations per
+    # pair forward and 120 more for the gradient; the pairs are counted from
+    # the candidates' projected vertices
+    _, _, _, uv = tr.eval_population_debug(P, Mp)
+    _, tris, _ = sc.flat()
+    u = uv[:, :, 0].double().cpu().numpy() + sc.K.cx
+    v = uv[:, :, 1].double().cpu().numpy() + sc.K.cy
+    cut = 14.0 * 1.0
+    ut, vt = u[:, tris], v[:, tris]
+    j0 = np.clip(np.ceil(ut.min(2) - cut), 0, None); j1 = np.clip(np.floor(ut.max(2) + cut), None, sc.K.width - 1)
+    i0 = np.clip(np.ceil(vt.min(2) - cut), 0, None); i1 = np.clip(np.floor(vt.max(2) + cut), None, sc.K.height - 1)
+    pairs = float((np.clip(j1 - j0 + 1, 0, None) * np.clip(i1 - i0 + 1, 0, None)).sum())
+    fp32_peak = 152 * 128 * 2.07e9
+    soft_roof = {"bound": "alu", "unit": "Tops/s", "peak": fp32_peak / 1e12,
+                 "peak_source": "152 SMs x 128 FP32 lanes/clk x 2070 MHz (derived)",
+                 "pairs_per_call": pairs, "ops_per_pair_forward": 60, "ops_per_pair_backward": 120,
+                 "achieved_forward": pairs * 60 / (fwd_ms / 1e3) / 1e12,
+                 "achieved_forward_backward": pairs * 180 / (bwd_ms / 1e3) / 1e12}
+    soft_roof["frac"] = soft_roof["achieved_forward_backward"] / soft_roof["peak"]
     n = min(n_frames, packed.shape[0])
     scales = wl.default_scales(9)
 
@@ -481,6 +522,7 @@ def bench_soft(a, rank, tr, sc, traj, init, packed, flush, n_frames: int = 60, r
     return {"workload": "640x512, %d-triangle mesh, sigma 1 px, cutoff 14 sigma, lambda=%d; tracking over %d frames "
                         "(errors after frame 5)" % (sc.n_tris, LAM, n),
             "soft_forward_ms": fwd_ms, "soft_forward_backward_ms": bwd_ms, "binary_fitness_ms": hard_ms,
+            "roofline": soft_roof,
             "soft_candidate_grads_per_s": LAM / (bwd_ms / 1e3),
             "track_cmaes_5gen": track(GENS, False), "track_cmaes_5gen_refine_top8_x10": track(GENS, True),
             "track_cmaes_10gen": track(2 * GENS, False),
@@ -810,17 +852,40 @@ def run_reference(a):
     print(json.dumps(out), flush=True)
 
 
-def run_profile_target():
-    """A short, fixed launch sequence for ncu captures of the fitness kernel."""
+def run_profile_target(form: str = "eval"):
+    """A short, fixed launch sequence for ncu captures of one kernel family."""
     import torch
 
     from paper_2603_11404_gb300 import api, build
     build.build()
+    if form in ("batch", "serve"):
+        _profile_forms(form)
+        return
     sc, traj, init = _workload(0, 1)
-    tr = api.Tracker(sc, loss_kind=wl.LOSS_ONE_MINUS_IOU, lambda_max=LAM)
+    if form == "pack":
+        tr = api.Tracker(sc, loss_kind=wl.LOSS_ONE_MINUS_IOU, lambda_max=1)
+        M = torch.from_numpy(_corrupt(np.zeros((sc.K.height, sc.K.width), np.uint8), 0, 0)).cuda()
+        for _ in range(6):
+            tr.pack_mask(M)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_target": "k_pack_mask 640x512"}))
+        return
+    tr = api.Tracker(sc, loss_kind=wl.LOSS_ONE_MINUS_IOU, lambda_max=LAM, raster=2 if form == "binned" else 0)
     S = api.unpack_mask(tr.render(torch.from_numpy(traj[0].astype(np.float32)).cuda()), sc.K.width).cpu().numpy()
     Mp = tr.pack_mask(torch.from_numpy(_corrupt(S, 0, 0)).cuda())
     P = torch.from_numpy(wl.population_around(np.random.default_rng(SEED), traj[0], LAM)).cuda()
+    if form == "soft":
+        for _ in range(3):
+            tr.soft_eval(P[:16].contiguous(), Mp, grad=True)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_target": "soft silhouette 640x512 lambda=16, forward + backward"}))
+        return
+    if form == "binned":
+        for _ in range(5):
+            tr.eval_population(P, Mp)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_target": "binned rasteriser 640x512 lambda=64", "kernel_digest": _kernel_digest()}))
+        return
     for _ in range(5):  # launches 2..4 of k_eval (0-based, after the render) are the measured ones
         tr.eval_population(P, Mp)
     es = api.CMAES(tr, LAM, traj[0], wl.default_scales(9), sigma0=1.0, seed=SEED)
@@ -832,10 +897,63 @@ def run_profile_target():
     print(json.dumps({"profile_target": "k_eval 640x512 lambda=64", "kernel_digest": _kernel_digest()}))
 
 
+def _profile_forms(form: str):
+    """The batch (3 tracked frames of the 24 uneven instances, launch shape
+    8 CTAs x 256 threads, no autotuning) or the server (8 streams, 12 frames
+    each, all submitted at once)."""
+    import torch
+
+    from paper_2603_11404_gb300 import api
+    if form == "batch":
+        rng = np.random.default_rng(SEED + 31)
+        inst = []
+        for spec in batching_instances():
+            sc = wl.make_scene(spec["mesh"], "c2", n_instruments=spec["n_inst"], K=spec["K"])
+            p0 = np.concatenate([wl.sample_state(rng, sc.K) for _ in range(spec["n_inst"])])
+            traj = wl.sinusoidal_trajectory(rng, p0, 3)
+            tr = api.Tracker(sc, loss_kind=wl.LOSS_ONE_MINUS_IOU, lambda_max=spec["lam"])
+            masks = [tr.pack_mask(torch.from_numpy(m).cuda()) for m in _masks_for(api, tr, sc, traj, rng)]
+            inst.append(dict(sc=sc, tr=tr, p0=p0, lam=spec["lam"], masks=masks))
+        opts = [api.CMAES(x["tr"], x["lam"], x["p0"], wl.default_scales(x["sc"].d), sigma0=1.0, seed=SEED + i,
+                          block_diag=x["sc"].d == 18) for i, x in enumerate(inst)]
+        b = api.Batch([x["tr"] for x in inst], optimisers=opts)
+        poses = [torch.empty(x["sc"].d, dtype=torch.float32, device="cuda") for x in inst]
+        for f in range(3):
+            b.track_frame([x["masks"][f] for x in inst], GENS, poses=poses)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_target": "k_eval_batch, 24 uneven instances"}))
+        return
+    rng = np.random.default_rng(SEED + 77)
+    srv = api.Server(max_active=SERVE_STREAMS, max_streams=SERVE_STREAMS, max_pending=64, max_pixels=640 * 512,
+                     max_lambda=LAM)
+    frames = []
+    for k in range(SERVE_STREAMS):
+        bim = k % 2 == 1
+        sc = wl.make_scene("c2", "c2", n_instruments=2 if bim else 1)
+        p0 = np.concatenate([wl.sample_state(rng, sc.K) for _ in range(sc.n_instruments)])
+        tr = api.Tracker(sc, loss_kind=wl.LOSS_ONE_MINUS_IOU, lambda_max=LAM)
+        masks = _masks_for(api, tr, sc, wl.sinusoidal_trajectory(rng, p0, 12), rng)
+        es = api.CMAES(tr, LAM, p0, wl.default_scales(sc.d), sigma0=1.0, seed=SEED + k, block_diag=bim)
+        sid = srv.add_stream(es, GENS, use_joint_reading=False)
+        frames.append((sid, masks, tr, es))
+    done, total = 0, SERVE_STREAMS * 12
+    pending = [(sid, m) for f in range(12) for sid, masks, _, _ in frames for m in [masks[f]]]
+    for _ in range(100000):  # a bound on the host loop (every frame finishes after its ticks)
+        if done >= total:
+            break
+        while pending and srv.submit(pending[0][0], pending[0][1], None, tag=0):
+            pending.pop(0)
+        act, q = srv.step()
+        done += len(srv.poll())
+        if act == 0 and q == 0 and not pending:
+            done += len(srv.poll(wait=True))
+    print(json.dumps({"profile_target": "server ticks, 8 streams x 12 frames"}))
+
+
 if __name__ == "__main__":
     args = _args()
     if args.profile_target:
-        run_profile_target()
+        run_profile_target(args.profile_target)
         raise SystemExit(0)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

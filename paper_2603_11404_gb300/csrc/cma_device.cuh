@@ -257,7 +257,7 @@ __device__ __forceinline__ void onesided_jacobi_regs(float *Xc, int lane, CmaSta
     for (; sweeps < 12; ++sweeps) {
         bool rotated = false;
         float rho = 0.0f;
-#pragma unroll 1
+#pragma unroll
         for (int r = 0; r < N2 - 1; ++r) {
             int partner = lane;
             if (lane < N2) {
@@ -272,20 +272,36 @@ __device__ __forceinline__ void onesided_jacobi_regs(float *Xc, int lane, CmaSta
             for (int q = 0; q < D; ++q) px[q] = __shfl_sync(0xffffffffu, x[q], src);
             if (act) {
                 const bool is_lo = lane < partner;
-                float a = 0.0f, b = 0.0f, g = 0.0f;  // |u|^2, |w|^2, u . w with u = lo, w = hi
+                // |u|^2, |w|^2, u . w (u = lo, w = hi), each as two interleaved chains
+                float a0 = 0.0f, a1 = 0.0f, b0 = 0.0f, b1 = 0.0f, g0 = 0.0f, g1 = 0.0f;
 #pragma unroll
-                for (int q = 0; q < D; ++q) {
+                for (int q = 0; q < D; q += 2) {
                     const float u = is_lo ? x[q] : px[q], w = is_lo ? px[q] : x[q];
-                    a = fmaf(u, u, a);
-                    b = fmaf(w, w, b);
-                    g = fmaf(u, w, g);
+                    a0 = fmaf(u, u, a0);
+                    b0 = fmaf(w, w, b0);
+                    g0 = fmaf(u, w, g0);
+                    if (q + 1 < D) {
+                        const float u1 = is_lo ? x[q + 1] : px[q + 1], w1 = is_lo ? px[q + 1] : x[q + 1];
+                        a1 = fmaf(u1, u1, a1);
+                        b1 = fmaf(w1, w1, b1);
+                        g1 = fmaf(u1, w1, g1);
+                    }
                 }
+                const float a = a0 + a1, b = b0 + b1, g = g0 + g1;
                 if (g * g > 1e-10f * a * b + floor2) {
-                    // approximate intrinsics are enough: any rotation close to the
-                    // annihilating one converges, and the test above uses exact g, a, b
-                    const float zeta = __fdividef(b - a, 2.0f * g), h = fmaf(zeta, zeta, 1.0f);
-                    const float t = copysignf(__fdividef(1.0f, fabsf(zeta) + h * rsqrtf(h)), zeta);
-                    const float c = rsqrtf(1.0f + t * t), sn = t * c;
+                    // the rotation that makes u . w = 0, by its double angle:
+                    // cos 2th = |b - a| / h, sin 2th = sgn((b - a) g) 2|g| / h with
+                    // h = sqrt((b - a)^2 + 4 g^2), |th| <= pi/4; then
+                    // c = sqrt((1 + cos 2th) / 2), s = sin 2th / (2 c) -- two
+                    // reciprocal square roots in sequence.  Approximate intrinsics
+                    // are enough: any rotation close to the annihilating one
+                    // converges, and the test above uses exact g, a, b
+                    const float dba = b - a;
+                    const float ih = rsqrtf(fmaf(dba, dba, 4.0f * g * g));
+                    const float c2 = fmaf(0.5f * fabsf(dba), ih, 0.5f);  // (1 + cos 2th) / 2, in [1/2, 1]
+                    const float ic = rsqrtf(c2);
+                    const float c = c2 * ic;
+                    const float sn = copysignf(1.0f, dba) * g * ih * ic;  // sin 2th / (2 c)
                     rotated = true;
                     rho = fmaxf(rho, fabsf(g) * rsqrtf(a * b));
                     const float cu = is_lo ? c : sn, cw = is_lo ? -sn : c;  // own = cu u + cw w
@@ -348,8 +364,16 @@ __device__ __forceinline__ void cma_tell_impl(const CmaConst &k, CmaState *st, c
     }
     for (int r = tid; r < mu; r += nt) S.w[r] = k.w[r];
     __syncthreads();
-    // stable ranking by (loss, index)
+    // stable ranking by (loss, index); a candidate that is selected (rank < mu)
+    // stages its step y in shared memory at its rank when the selected steps
+    // fit (its loads are issued before the ranking count, which hides them)
+    const bool staged = mu * d <= kYselCap;
     for (int i = tid; i < lam; i += nt) {
+        double yi[kMaxD];
+        if (staged)
+#pragma unroll
+            for (int q = 0; q < kMaxD; ++q)
+                if (q < d) yi[q] = y[(size_t)i * d + q];
         float li = S.sl[i];
         int r = 0;
         for (int j = 0; j < lam; ++j) {
@@ -357,6 +381,10 @@ __device__ __forceinline__ void cma_tell_impl(const CmaConst &k, CmaState *st, c
             r += (lj < li) || (lj == li && j < i);
         }
         S.order[r] = i;
+        if (staged && r < mu)
+#pragma unroll
+            for (int q = 0; q < kMaxD; ++q)
+                if (q < d) S.ysel[r * d + q] = yi[q];
     }
     __syncthreads();
     if (tid == 0) {
@@ -366,14 +394,6 @@ __device__ __forceinline__ void cma_tell_impl(const CmaConst &k, CmaState *st, c
             for (int i = 0; i < d; ++i) st->best_x[i] = params[(size_t)b * d + i];
         }
     }
-    // the selected steps y_{r:lam}, r < mu, staged in shared memory when they fit
-    const bool staged = mu * d <= kYselCap;
-    if (staged)
-        for (int e = tid; e < mu * d; e += nt) {
-            int r = e / d, i = e - r * d;
-            S.ysel[e] = y[(size_t)S.order[r] * d + i];
-        }
-    __syncthreads();
 #define YSEL(r, i) (staged ? S.ysel[(r) * d + (i)] : y[(size_t)S.order[r] * d + (i)])
     // <y>_w = sum_{r < mu} w_r y_{r:lam}: 8 deterministic partial sums per coordinate
     const int chunk = (mu + 7) / 8;
@@ -428,9 +448,15 @@ __device__ __forceinline__ void cma_tell_impl(const CmaConst &k, CmaState *st, c
     {
         double *part4[4] = {S.A, S.A2, S.V, S.V2};
         const int rchunk = (mu + 3) / 4;
-        for (int e = tid; e < 4 * dd; e += nt) {
-            int pr = e / dd, ij = e - pr * dd, i = ij / d, j = ij - i * d;
-            if (j < i) continue;
+        const int nup = d * (d + 1) / 2;  // entries (i, j), j >= i
+        for (int e = tid; e < 4 * nup; e += nt) {
+            const int pr = e / nup;
+            int u = e - pr * nup, i = 0;
+            while (u >= d - i) {  // row i holds d - i entries of the upper triangle
+                u -= d - i;
+                ++i;
+            }
+            const int j = i + u, ij = i * d + j;
             double rmu = 0.0;
             int r1 = min(mu, (pr + 1) * rchunk);
             for (int r = pr * rchunk; r < r1; ++r) rmu = __fma_rn(S.w[r] * YSEL(r, i), YSEL(r, j), rmu);

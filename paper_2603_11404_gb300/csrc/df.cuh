@@ -11,7 +11,8 @@
 //
 // sin/cos: Cody-Waite reduction by pi/2 split into a float with few bits (so
 // n * P1 is exact) and a double-float remainder, then the Taylor series of sin
-// and cos on [-pi/4, pi/4] to the 17th / 18th power by Horner's rule.
+// and cos on [-pi/4, pi/4] to the 17th / 18th power, evaluated by Estrin's
+// scheme (independent pairs, then the powers u^2, u^4, u^8).
 #pragma once
 
 #include <math.h>
@@ -93,17 +94,28 @@ __device__ __forceinline__ dfl df_sqrt(dfl a)
 // hi/lo split of a double done by the compiler (constant expressions only).
 #define DFL_CONST(x) dfl{(float)(x), (float)((x) - (double)(float)(x))}
 
-// Taylor coefficients as double-float constants: (-1)^j/(2j+1)! and (-1)^j/(2j)!.
-#define DFL_C2(x) {(float)(x), (float)((x) - (double)(float)(x))}
-static __constant__ float2 kSinTaylor[9] = {
-    DFL_C2(1.0), DFL_C2(-1.0 / 6.0), DFL_C2(1.0 / 120.0), DFL_C2(-1.0 / 5040.0), DFL_C2(1.0 / 362880.0),
-    DFL_C2(-1.0 / 39916800.0), DFL_C2(1.0 / 6227020800.0), DFL_C2(-1.0 / 1307674368000.0),
-    DFL_C2(1.0 / 355687428096000.0)};
-static __constant__ float2 kCosTaylor[10] = {
-    DFL_C2(1.0), DFL_C2(-1.0 / 2.0), DFL_C2(1.0 / 24.0), DFL_C2(-1.0 / 720.0), DFL_C2(1.0 / 40320.0),
-    DFL_C2(-1.0 / 3628800.0), DFL_C2(1.0 / 479001600.0), DFL_C2(-1.0 / 87178291200.0),
-    DFL_C2(1.0 / 20922789888000.0), DFL_C2(-1.0 / 6402373705728000.0)};
-#undef DFL_C2
+// Taylor coefficients (-1)^j/(2j+1)! and (-1)^j/(2j)! as double-float
+// constants folded into the instructions (no constant-bank loads: the first
+// evaluation in a CTA would otherwise wait on constant-cache misses).
+#define TS0 DFL_CONST(1.0)
+#define TS1 DFL_CONST(-1.0 / 6.0)
+#define TS2 DFL_CONST(1.0 / 120.0)
+#define TS3 DFL_CONST(-1.0 / 5040.0)
+#define TS4 DFL_CONST(1.0 / 362880.0)
+#define TS5 DFL_CONST(-1.0 / 39916800.0)
+#define TS6 DFL_CONST(1.0 / 6227020800.0)
+#define TS7 DFL_CONST(-1.0 / 1307674368000.0)
+#define TS8 DFL_CONST(1.0 / 355687428096000.0)
+#define TC0 DFL_CONST(1.0)
+#define TC1 DFL_CONST(-1.0 / 2.0)
+#define TC2 DFL_CONST(1.0 / 24.0)
+#define TC3 DFL_CONST(-1.0 / 720.0)
+#define TC4 DFL_CONST(1.0 / 40320.0)
+#define TC5 DFL_CONST(-1.0 / 3628800.0)
+#define TC6 DFL_CONST(1.0 / 479001600.0)
+#define TC7 DFL_CONST(-1.0 / 87178291200.0)
+#define TC8 DFL_CONST(1.0 / 20922789888000.0)
+#define TC9 DFL_CONST(-1.0 / 6402373705728000.0)
 
 struct dfl2 {
     dfl s, c;
@@ -125,18 +137,14 @@ static __device__ __noinline__ dfl2 df_sincos(dfl x)
     // u = r^2, evaluated by Estrin's scheme (independent pairs, then powers
     // u^2, u^4, u^8) to keep the dependent chain short
     const dfl u2 = df_mul(u, u), u4 = df_mul(u2, u2), u8 = df_mul(u4, u4);
-#define TS(j) dfl{kSinTaylor[j].x, kSinTaylor[j].y}
-#define TC(j) dfl{kCosTaylor[j].x, kCosTaylor[j].y}
-    dfl s01 = df_fma(TS(1), u, TS(0)), s23 = df_fma(TS(3), u, TS(2));
-    dfl s45 = df_fma(TS(5), u, TS(4)), s67 = df_fma(TS(7), u, TS(6));
-    dfl c01 = df_fma(TC(1), u, TC(0)), c23 = df_fma(TC(3), u, TC(2));
-    dfl c45 = df_fma(TC(5), u, TC(4)), c67 = df_fma(TC(7), u, TC(6)), c89 = df_fma(TC(9), u, TC(8));
+    dfl s01 = df_fma(TS1, u, TS0), s23 = df_fma(TS3, u, TS2);
+    dfl s45 = df_fma(TS5, u, TS4), s67 = df_fma(TS7, u, TS6);
+    dfl c01 = df_fma(TC1, u, TC0), c23 = df_fma(TC3, u, TC2);
+    dfl c45 = df_fma(TC5, u, TC4), c67 = df_fma(TC7, u, TC6), c89 = df_fma(TC9, u, TC8);
     dfl s03 = df_fma(s23, u2, s01), s47 = df_fma(s67, u2, s45);
     dfl c03 = df_fma(c23, u2, c01), c47 = df_fma(c67, u2, c45);
-    dfl ps = df_fma(TS(8), u8, df_fma(s47, u4, s03));
+    dfl ps = df_fma(TS8, u8, df_fma(s47, u4, s03));
     dfl pc = df_fma(c89, u8, df_fma(c47, u4, c03));
-#undef TS
-#undef TC
     dfl sr = df_mul(ps, r);
     dfl cr = pc;
     int q = ((int)n) & 3;

@@ -615,6 +615,21 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft_reduce(SoftArgs a)
     for (int e = tid; e < a.nF * 12; e += blockDim.x) G[e] = 0ull;
     __syncthreads();
     const size_t base = ((size_t)c * a.nI + b) * a.V;
+    // each thread sums its vertices' terms in registers while their frame stays
+    // the same (a link's vertices are contiguous), then adds them to G: the
+    // integer sums are exact, so grouping them changes nothing
+    long long acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = 0;
+    int fcur = -1;
+    auto flush = [&]() {
+        if (fcur < 0) return;
+#pragma unroll
+        for (int k = 0; k < 12; ++k)
+            if (acc[k]) atomicAdd(G + fcur * 12 + k, (unsigned long long)acc[k]);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[k] = 0;
+    };
     for (int v = tid; v < a.V; v += blockDim.x) {
         const float4 s = a.sv[base + v];
         const longlong2 q = a.gv[base + v];
@@ -623,15 +638,20 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft_reduce(SoftArgs a)
         const float iz = 1.0f / s.z;
         const float gX = gx * a.fx * iz, gY = gy * a.fy * iz, gZ = -(gx * s.x + gy * s.y) * iz;
         const float4 p = a.verts[v];
-        unsigned long long *Gf = G + (int)p.w * 12;
+        const int f = (int)p.w;
+        if (f != fcur) {
+            flush();
+            fcur = f;
+        }
         const float vh[4] = {p.x, p.y, p.z, 1.0f};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            atomicAdd(Gf + k, (unsigned long long)to_fixed(gX * vh[k], kGScale));
-            atomicAdd(Gf + 4 + k, (unsigned long long)to_fixed(gY * vh[k], kGScale));
-            atomicAdd(Gf + 8 + k, (unsigned long long)to_fixed(gZ * vh[k], kGScale));
+            acc[k] += to_fixed(gX * vh[k], kGScale);
+            acc[4 + k] += to_fixed(gY * vh[k], kGScale);
+            acc[8 + k] += to_fixed(gZ * vh[k], kGScale);
         }
     }
+    flush();
     __syncthreads();
     if (tid < 9) {
         float acc = 0.0f;
