@@ -67,7 +67,7 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-forms", action="store_true", help="skip the batching and serving measurements")
     p.add_argument("--serve-frames", type=int, default=1000, help="frames per camera stream in the serving run")
-    p.add_argument("--long-frames", type=int, default=2500,
+    p.add_argument("--long-frames", type=int, default=3200,
                    help="frames of the longer run that reports the spread of the frame time")
     p.add_argument("--profile-target", nargs="?", const="eval", default=None,
                    choices=["eval", "binned", "soft", "batch", "serve", "pack"],

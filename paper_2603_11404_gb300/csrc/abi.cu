@@ -295,9 +295,9 @@ trk_status tracker_create(const trk_link_mesh *meshes, int32_t n_meshes, const t
         return inval("image or mesh too large for the binned rasteriser");
     }
     // AUTO takes the cluster-bitmap kernel, the faster of the two on every
-    // workload measured (640 x 512, 20k triangles: 47 us against 80 us for 64
-    // candidates, 524 against 798 us for 1024), and the binned form only for an
-    // image whose bitmap does not fit one CTA's shared memory
+    // workload measured (640 x 512, 20k triangles, 64 candidates: 43 us against
+    // 72.5 us), and the binned form only for an image whose bitmap does not fit
+    // one CTA's shared memory
     const bool cluster_fits = t->lc.smem <= 227 * 1024;
     if (cfg->raster == TRK_RASTER_BINNED)
         t->raster = TRK_RASTER_BINNED;
