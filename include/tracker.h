@@ -386,7 +386,9 @@ trk_status soft_refine(trk_cmaes *es, const uint32_t *mask_packed_dev, int32_t t
 /* ---------------------------------------------------------------------------
  * Heterogeneous batches: many instances (one- or two-instrument scenes with
  * their own meshes, image sizes and population sizes) in one persistent launch
- * per generation.  Not a paper feature: the paper tracks one scene per call;
+ * per generation and image-size group (instances whose shared-memory bitmaps
+ * allow the same number of CTAs per SM form a group; the groups' launches run
+ * side by side).  Not a paper feature: the paper tracks one scene per call;
  * batching serves several scenes or camera streams per GPU pass.
  * ------------------------------------------------------------------------- */
 typedef struct trk_batch trk_batch;
@@ -402,7 +404,7 @@ trk_status batch_create(trk_tracker *const *trackers, trk_cmaes *const *optimise
 trk_status batch_destroy(trk_batch *b);
 
 /* Launch shape of the persistent kernel: set, or read back (n_clusters = the
- * co-resident clusters of the persistent grid). */
+ * clusters of the persistent grids, summed over the image-size groups). */
 trk_status batch_set_launch(trk_batch *b, int32_t cluster, int32_t threads);
 trk_status batch_get_launch(const trk_batch *b, int32_t *cluster, int32_t *threads, int32_t *n_clusters);
 

@@ -4,7 +4,12 @@
 //
 //   k_eval_batch   a fixed grid of co-resident clusters pulls (instance,
 //                  candidate) items, largest instances first, from an atomic
-//                  queue; each item is the single-candidate fitness body
+//                  queue; each item is the single-candidate fitness body.
+//                  Instances are grouped by how many CTAs of their shared-
+//                  memory bitmap fit an SM, and each group has its own grid,
+//                  queue and bitmap size (the groups' launches run side by
+//                  side on forked streams), so a small image is not held to
+//                  the occupancy of the batch's largest one
 //   cma batch      the CMA-ES update of every instance in one launch, one CTA
 //                  per instance (the updates run side by side on the SMs)
 //
@@ -33,9 +38,19 @@ struct trk_batch {
     EvalArgs *descs = nullptr;          // [n] device
     const uint32_t **masks = nullptr;   // [n] device table
     float **poses = nullptr;            // [n] device table
-    int2 *items = nullptr;              // [n_items] device, largest instances first
+    int2 *items = nullptr;              // [n_items] device: by group, largest instances first in each
     int n_items = 0;
-    unsigned *next_item = nullptr;
+    unsigned *next_item = nullptr;      // [groups] device queue heads
+    struct Group {
+        int item_off = 0, n_items = 0;
+        size_t smem = 0;                // the largest bitmap of the group's instances
+        LaunchCfg lc{};
+        int n_clusters = 0;
+    };
+    std::vector<Group> groups;          // largest shared-memory footprint first
+    std::vector<cudaStream_t> aux;      // [groups - 1] streams the later groups launch on
+    std::vector<cudaEvent_t> joined;    // [groups - 1] their completion
+    cudaEvent_t forked = nullptr;
     int2 *snap = nullptr;               // batch-owned scratch for every instance
     BatchTables tb;                     // CMA-ES tables (tb.pose aliases poses)
     const void **pin = nullptr;         // pinned staging for the two pointer tables
@@ -51,6 +66,11 @@ static void batch_free(trk_batch *b)
     if (!b) return;
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     if (b->cap) cudaStreamDestroy(b->cap);
+    for (cudaStream_t x : b->aux)
+        if (x) cudaStreamDestroy(x);
+    for (cudaEvent_t x : b->joined)
+        if (x) cudaEventDestroy(x);
+    if (b->forked) cudaEventDestroy(b->forked);
     cudaFree(b->descs);
     cudaFree(b->masks);
     cudaFree(b->poses);
@@ -73,7 +93,8 @@ static trk_status bfail(trk_status s, const char *why)
     return s;
 }
 
-// Shared memory and occupancy for a launch shape; fills b->lc and b->n_clusters.
+// Shared memory and occupancy for a launch shape, per group; fills the
+// groups' launch configurations, b->lc (the shape) and b->n_clusters (summed).
 static trk_status batch_configure(trk_batch *b, int cluster, int threads)
 {
     int max_inst = 1;
@@ -87,14 +108,22 @@ static trk_status batch_configure(trk_batch *b, int cluster, int threads)
     if (cluster <= 0) cluster = 8;
     if (cluster > 8) return bfail(TRK_EINVAL, "batch cluster must be 1..8");
     if (smem > 227 * 1024) return bfail(TRK_EINVAL, "largest image too large for the shared-memory bitmap");
-    int maxc = 0;
-    cudaError_t e = prepare_eval_batch(smem, cluster, threads, &maxc);
-    if (e != cudaSuccess) return bfail(TRK_ECUDA, cudaGetErrorString(e));
-    if (maxc <= 0) return bfail(TRK_EINVAL, "launch shape does not fit on the device");
+    int total = 0;
+    for (trk_batch::Group &g : b->groups) {
+        int maxc = 0;
+        cudaError_t e = prepare_eval_batch(g.smem, cluster, threads, &maxc);
+        if (e != cudaSuccess) return bfail(TRK_ECUDA, cudaGetErrorString(e));
+        if (maxc <= 0) return bfail(TRK_EINVAL, "launch shape does not fit on the device");
+        g.lc.cluster = cluster;
+        g.lc.threads = threads;
+        g.lc.smem = g.smem;
+        g.n_clusters = std::min(maxc, g.n_items);
+        total += g.n_clusters;
+    }
     b->lc.cluster = cluster;
     b->lc.threads = threads;
     b->lc.smem = smem;
-    b->n_clusters = std::min(maxc, b->n_items);
+    b->n_clusters = total;
     if (b->gexec) {
         cudaGraphExecDestroy(b->gexec);
         b->gexec = nullptr;
@@ -140,7 +169,6 @@ trk_status batch_create(trk_tracker *const *trackers, trk_cmaes *const *optimise
         (e = cudaMalloc(&b->masks, sizeof(void *) * n)) != cudaSuccess ||
         (e = cudaMalloc(&b->poses, sizeof(void *) * n)) != cudaSuccess ||
         (e = cudaMalloc(&b->items, sizeof(int2) * b->n_items)) != cudaSuccess ||
-        (e = cudaMalloc(&b->next_item, sizeof(unsigned))) != cudaSuccess ||
         (e = cudaMalloc(&b->snap, sizeof(int2) * snap_total)) != cudaSuccess ||
         (e = cudaMalloc(&b->tb.k, sizeof(void *) * n)) != cudaSuccess ||
         (e = cudaMalloc(&b->tb.st, sizeof(void *) * n)) != cudaSuccess ||
@@ -195,15 +223,54 @@ trk_status batch_create(trk_tracker *const *trackers, trk_cmaes *const *optimise
         hni[i] = t->ch.n_inst;
         b->hdescs[i] = a;
     }
-    // items: (instance, candidate), instances with more work first
+    // groups: instances by the number of CTAs with their bitmap that fit an
+    // SM's shared memory (a few KB of other shared memory per CTA included),
+    // fewest first; items: (instance, candidate) by group, and within a group
+    // instances with more work first
+    int dev = 0, sm_smem = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess) {
+        batch_free(b);
+        set_last_error(cudaGetErrorString(e));
+        return TRK_ECUDA;
+    }
+    auto per_sm = [&](int i) { return (long long)sm_smem / (long long)(eval_smem_bytes(b->hdescs[i]) + 4096); };
+    auto cost = [&](int i) { return (long long)(b->tr[i]->V + b->tr[i]->T) * b->tr[i]->ch.n_inst; };
     std::vector<int> order(n);
     std::iota(order.begin(), order.end(), 0);
-    auto cost = [&](int i) { return (long long)(b->tr[i]->V + b->tr[i]->T) * b->tr[i]->ch.n_inst; };
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        const long long px = per_sm(x), py = per_sm(y);
+        return px != py ? px < py : cost(x) > cost(y);
+    });
     std::vector<int2> items;
     items.reserve(b->n_items);
-    for (int i : order)
+    for (int k = 0; k < n; ++k) {
+        const int i = order[k];
+        if (k == 0 || per_sm(i) != per_sm(order[k - 1])) {
+            b->groups.emplace_back();
+            b->groups.back().item_off = (int)items.size();
+        }
+        trk_batch::Group &g = b->groups.back();
+        g.n_items += b->lam[i];
+        g.smem = std::max(g.smem, eval_smem_bytes(b->hdescs[i]));
         for (int c = 0; c < b->lam[i]; ++c) items.push_back(make_int2(i, c));
+    }
+    const int G = (int)b->groups.size();
+    b->aux.assign(G - 1, nullptr);
+    b->joined.assign(G - 1, nullptr);
+    if ((e = cudaMalloc(&b->next_item, sizeof(unsigned) * G)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&b->forked, cudaEventDisableTiming)) != cudaSuccess) {
+        batch_free(b);
+        set_last_error(cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? TRK_ENOMEM : TRK_ECUDA;
+    }
+    for (int g = 0; g + 1 < G; ++g)
+        if ((e = cudaStreamCreateWithFlags(&b->aux[g], cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&b->joined[g], cudaEventDisableTiming)) != cudaSuccess) {
+            batch_free(b);
+            set_last_error(cudaGetErrorString(e));
+            return TRK_ECUDA;
+        }
     if ((e = cudaMemcpy(b->descs, b->hdescs.data(), sizeof(EvalArgs) * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(b->items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(b->tb.k, hk.data(), sizeof(void *) * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -268,14 +335,35 @@ static trk_status stage_eval(trk_batch *b, const float *const *params, const uin
     return e == cudaSuccess ? TRK_OK : bfail(TRK_ECUDA, cudaGetErrorString(e));
 }
 
+// One persistent fitness launch per group: the first group on s, the others
+// on streams forked from s and joined back into it (under stream capture the
+// fork and join become graph edges).
+static cudaError_t launch_groups(trk_batch *b, const uint32_t *const *masks, cudaStream_t s)
+{
+    const int G = (int)b->groups.size();
+    auto one = [&](int g, cudaStream_t st) {
+        const trk_batch::Group &x = b->groups[g];
+        return launch_eval_batch(b->descs, masks, b->items + x.item_off, x.n_items, b->next_item + g, x.lc,
+                                 x.n_clusters, st);
+    };
+    cudaError_t e = cudaMemsetAsync(b->next_item, 0, sizeof(unsigned) * G, s);
+    if (e != cudaSuccess) return e;
+    if (G > 1 && (e = cudaEventRecord(b->forked, s)) != cudaSuccess) return e;
+    for (int g = 1; g < G; ++g)
+        if ((e = cudaStreamWaitEvent(b->aux[g - 1], b->forked, 0)) != cudaSuccess ||
+            (e = one(g, b->aux[g - 1])) != cudaSuccess ||
+            (e = cudaEventRecord(b->joined[g - 1], b->aux[g - 1])) != cudaSuccess)
+            return e;
+    if ((e = one(0, s)) != cudaSuccess) return e;
+    for (int g = 1; g < G; ++g)
+        if ((e = cudaStreamWaitEvent(s, b->joined[g - 1], 0)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
 static trk_status launch_staged(trk_batch *b, cudaStream_t s)
 {
-    cudaError_t e;
-    if ((e = cudaMemsetAsync(b->next_item, 0, sizeof(unsigned), s)) != cudaSuccess ||
-        (e = launch_eval_batch(b->descs, nullptr, b->items, b->n_items, b->next_item, b->lc, b->n_clusters, s)) !=
-            cudaSuccess)
-        return bfail(TRK_ECUDA, cudaGetErrorString(e));
-    return TRK_OK;
+    cudaError_t e = launch_groups(b, nullptr, s);
+    return e == cudaSuccess ? TRK_OK : bfail(TRK_ECUDA, cudaGetErrorString(e));
 }
 
 trk_status batch_eval(trk_batch *b, const float *const *params_dev, const uint32_t *const *masks_dev,
@@ -297,10 +385,7 @@ static cudaError_t enqueue_frame(trk_batch *b, int generations, cudaStream_t s)
 {
     cudaError_t e = launch_cma_batch(0, b->n, nullptr, b->tb, s);
     for (int g = 0; g < generations && e == cudaSuccess; ++g) {
-        if ((e = cudaMemsetAsync(b->next_item, 0, sizeof(unsigned), s)) != cudaSuccess) break;
-        if ((e = launch_eval_batch(b->descs, b->masks, b->items, b->n_items, b->next_item, b->lc, b->n_clusters,
-                                   s)) != cudaSuccess)
-            break;
+        if ((e = launch_groups(b, b->masks, s)) != cudaSuccess) break;
         // the last generation's updates leave out the square roots (the next frame resets)
         e = launch_cma_batch(g == generations - 1 ? 3 : 1, b->n, nullptr, b->tb, s);
     }
