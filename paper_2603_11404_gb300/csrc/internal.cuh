@@ -148,7 +148,9 @@ struct CmaState {
     double sigma;
     double cs_pow;         // (1 - c_sigma)^(2 gen), for the h_sigma test
     int gen, gen_total;
-    int jacobi_sweeps, warn;
+    int jacobi_sweeps;     // sweeps of the last eigen-path update, or minus its Newton-Schulz steps
+    int warn;              // bit 0: an eigenvalue was not positive; bit 1: Newton-Schulz did not
+                           // converge, the eigen path serves until the next reset
     float best_loss;       // best of the current frame (since the last reset)
     float best_x[kMaxD];
     // double-float copies for the sampler (FP32 pipes): C^(1/2), mean, sigma

@@ -60,11 +60,10 @@ def test_ask_tell_state_parity(api, d, lam, block):
         o.tell(loss)
         st = g.state()
         assert st["gen"] == o.gen and st["gen_total"] == o.gen_total
-        # The device square roots are accurate to ~1e-12 relative (an FP32
-        # Jacobi pass, then Newton-Schulz orthogonalisation and Newton
-        # square-root steps in FP64).  Perturbing the oracle's C by 1e-12
-        # relative before every decomposition moves its state by ~1e-11 after
-        # 25 generations, so 1e-9 leaves a wide margin.
+        # The device square roots are accurate to ~1e-14 relative (the
+        # coupled Newton-Schulz iteration in FP64).  Perturbing the oracle's C
+        # by 1e-12 relative before every decomposition moves its state by
+        # ~1e-11 after 25 generations, so 1e-9 leaves a wide margin.
         assert _rel(st["m"], o.m) < 1e-9
         assert abs(st["sigma"] - o.sigma) / o.sigma < 1e-9
         assert _rel(st["C"], o.C) < 1e-9
@@ -74,6 +73,42 @@ def test_ask_tell_state_parity(api, d, lam, block):
             assert np.all(st["C"][:9, 9:] == 0) and np.all(st["C"][9:, :9] == 0)
         assert np.array_equal(st["C"], st["C"].T)
     assert n_ulp_diff <= 3 + lam * d * 25 // 5000  # one-ulp sampling differences at rounding ties are rare
+
+
+def test_square_roots_stay_exact_on_an_ill_conditioned_quadratic(api):
+    """A quadratic whose curvatures span 12 decades: the covariance learns a
+    condition number above 1e10 within 500 generations, where an FP32
+    eigenvalue pass no longer resolves the small eigenvalues.  The device
+    state (its square roots by the Newton-Schulz iteration) stays within 1e-9
+    of the FP64 oracle fed the same normals all the way, and the stored square
+    roots satisfy C^(1/2) C^(1/2) = C and C^(1/2) C^(-1/2) = I (read from the
+    save blob: a 24-byte header, then m, p_sigma, p_c [18], C, B [324], ev [18],
+    C^(1/2), C^(-1/2) [324] as doubles, row-major d x d at the front)."""
+    sc = wl.make_scene("c1", "c1")
+    tr = api.Tracker(sc, lambda_max=16)
+    wts = 10.0 ** np.linspace(0, 12, 9)
+    g = api.CMAES(tr, 16, np.ones(9), np.ones(9), sigma0=1.0, seed=3)
+    o = OCMAES(9, 16, np.ones(9), np.ones(9), sigma0=1.0, seed=3)
+    for gen in range(500):
+        z = o.normals()
+        g.ask_normals(torch.from_numpy(z).cuda())
+        loss = ((o.ask(z).astype(np.float64) ** 2) @ wts).astype(np.float32)
+        g.tell(torch.from_numpy(loss).cuda())
+        o.tell(loss)
+        if gen % 100 == 99:
+            st = g.state()
+            assert _rel(st["m"], o.m) < 1e-9, gen
+            assert _rel(st["C"], o.C) < 1e-9, gen
+            assert abs(st["sigma"] - o.sigma) / o.sigma < 1e-9, gen
+    ev = np.linalg.eigvalsh(o.C)
+    assert ev.max() / ev.min() > 1e10
+    dbl = np.frombuffer(g.save()[24:24 + 8 * 1388], np.float64)
+    C = dbl[54:54 + 81].reshape(9, 9)
+    Ch = dbl[720:720 + 81].reshape(9, 9)
+    Ci = dbl[1044:1044 + 81].reshape(9, 9)
+    assert _rel(C, o.C) < 1e-9
+    assert _rel(Ch @ Ch, C) < 1e-12
+    assert np.abs(Ch @ Ci - np.eye(9)).max() < 1e-12
 
 
 @pytest.mark.parametrize("d,lam", [(9, 64), (18, 32)])
