@@ -500,11 +500,16 @@ __device__ __forceinline__ void cma_tell_impl(const CmaConst &k, CmaState *st, c
 // A = C / c, Y_0 = A and Z_0 = I,
 //     T_k = (3 I - Z_k Y_k) / 2,   Y_{k+1} = Y_k T_k,   Z_{k+1} = T_k Z_k,
 // Y_k -> A^(1/2) and Z_k -> A^(-1/2), quadratically once close, whenever the
-// eigenvalues of A lie in (0, 3).  c = max(trace C / d, r / 2.5), r the
-// largest absolute row sum of C (a bound on its largest eigenvalue), puts
-// them in (0, 2.5] and makes A = I when C is a multiple of I.  Every iterate
-// is a polynomial in C, so FP64 rounding stays at the level of the result
-// (no eigenvector step whose errors would freeze in); the residual of a
+// eigenvalues of A lie in (0, 3).  c is the power of two at or above
+// max(trace C / d, r / 2.5), r the largest absolute row sum of C (a bound on
+// its largest eigenvalue; the target is taken in FP32 with a little margin):
+// the eigenvalues land in (0, 2.5], C = I gives A = I, and dividing by c and
+// multiplying by sqrt(c) cost no rounding and no FP64 division or square
+// root.  Every iterate is a polynomial in C, so FP64 rounding stays at the
+// level of the result (no eigenvector step whose errors would freeze in; the
+// iterates are not symmetrised: a numpy prototype that mirrored the upper
+// triangles of both T and Y, Z diverged from condition number 1e6 on,
+// although mirroring either alone converged); the residual of a
 // numpy prototype on d = 9 was 3e-15 for condition numbers up to 10, 1e-13
 // at 1e3, 1e-10 at 1e6, in 6, 13 and 22 steps (on the GPU: 29 steps and
 // 2e-15 at 4e8, where the eigen path's FP32 Jacobi pass no longer resolves
@@ -541,25 +546,25 @@ __device__ __forceinline__ bool cma_sqrt_newton_schulz(const CmaConst &k, CmaSta
     double *Y = S.A, *Z = kPacked ? S.A + dd : S.V, *Y2 = kPacked ? S.A + 2 * dd : S.V2,
            *Z2 = kPacked ? S.A + 3 * dd : S.B, *T = S.A2;
     const double *C = S.C;
-    if (tid < 32) {  // the scale c
-        double tr = 0.0, row = 0.0;
+    if (tid < 32) {  // the scale c = 2^e, chosen in FP32 (kept in S.part[1][0])
+        float tr = 0.0f, row = 0.0f;
         if (tid < d) {
-            tr = C[tid * d + tid];
-            for (int q = 0; q < d; ++q) row = __dadd_rn(row, fabs(C[tid * d + q]));
+            tr = (float)C[tid * d + tid];
+            for (int q = 0; q < d; ++q) row += fabsf((float)C[tid * d + q]);
         }
         for (int o = 16; o; o >>= 1) {
-            tr = __dadd_rn(tr, __shfl_xor_sync(0xffffffffu, tr, o));
-            row = fmax(row, __shfl_xor_sync(0xffffffffu, row, o));
+            tr += __shfl_xor_sync(0xffffffffu, tr, o);
+            row = fmaxf(row, __shfl_xor_sync(0xffffffffu, row, o));
         }
         if (tid == 0) {
-            const double c = fmax(tr / d, row / 2.5);
-            S.part[1][0] = 1.0 / c;
-            S.part[1][1] = sqrt(c);
-            S.part[1][2] = 1.0 / S.part[1][1];
+            int e = 0;
+            const float m = frexpf(fmaxf(tr / d, 1.0001f * row / 2.5f), &e);  // target = m 2^e, m in [1/2, 1)
+            S.part[1][0] = (m > 0.0f) ? (double)e : 0.0;
         }
     }
     __syncthreads();
-    const double ic = S.part[1][0];
+    const int e2 = (int)S.part[1][0];
+    const double ic = ldexp(1.0, -e2);
     for (int e = tid; e < dd; e += nt) {
         Y[e] = __dmul_rn(C[e], ic);
         Z[e] = (e / d == e % d) ? 1.0 : 0.0;
@@ -594,9 +599,10 @@ __device__ __forceinline__ bool cma_sqrt_newton_schulz(const CmaConst &k, CmaSta
         }
         return false;
     }
-    // outputs: C^(1/2) = sqrt(c) Y, C^(-1/2) = Z / sqrt(c), symmetrised; the
+    // outputs: C^(1/2) = sqrt(c) Y, C^(-1/2) = Z / sqrt(c) (sqrt(c) a power of
+    // two, times sqrt 2 for odd e), symmetrised; the
     // step size on a thread that has no entry (FP64 exp off the critical path)
-    const double sc = S.part[1][1], isc = S.part[1][2];
+    const double sc = ldexp((e2 & 1) ? M_SQRT2 : 1.0, e2 >> 1), isc = ldexp((e2 & 1) ? M_SQRT1_2 : 1.0, -(e2 >> 1));
     for (int e = tid; e < dd; e += nt) {
         const int i = e / d, j = e - i * d;
         if (j < i) continue;
