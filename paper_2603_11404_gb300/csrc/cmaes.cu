@@ -85,7 +85,12 @@ __global__ void k_cma_finish(const CmaConst *__restrict__ kp, CmaState *st, floa
 
 // Batched forms: block b serves instance sel[b] (or b when sel is NULL) of
 // tables of device pointers indexed by instance.
-__device__ __forceinline__ int batch_instance(const int *sel) { return sel ? sel[blockIdx.x] : (int)blockIdx.x; }
+// Selected entries may carry kSelNoSqrt (op 4: that instance's update leaves
+// out the square roots).
+__device__ __forceinline__ int batch_instance(const int *sel)
+{
+    return sel ? (sel[blockIdx.x] & ~kSelNoSqrt) : (int)blockIdx.x;
+}
 
 __global__ void k_cma_reset_batch(const int *sel, const CmaConst *const *kp, CmaState *const *st, const int *n_inst,
                                   const float *const *joint)
@@ -101,7 +106,8 @@ __global__ void __launch_bounds__(kTellThreads) k_cma_tell_batch(const int *sel,
 {
     __shared__ TellSmem S;
     const int i = batch_instance(sel);
-    cma_tell_block(*kp[i], st[i], y[i], params[i], loss[i], S, threadIdx.x, blockDim.x, do_sqrt != 0);
+    const bool sq = do_sqrt == 2 ? !(sel[blockIdx.x] & kSelNoSqrt) : do_sqrt != 0;
+    cma_tell_block(*kp[i], st[i], y[i], params[i], loss[i], S, threadIdx.x, blockDim.x, sq);
 }
 
 __global__ void k_cma_finish_batch(const int *sel, const CmaConst *const *kp, CmaState *const *st,
@@ -115,7 +121,8 @@ cudaError_t launch_cma_batch(int op, int n, const int *sel, const BatchTables &t
 {
     if (n == 0) return cudaSuccess;
     if (op == 0) k_cma_reset_batch<<<n, 128, 0, s>>>(sel, t.k, t.st, t.ninst, t.joint);
-    if (op == 1 || op == 3) k_cma_tell_batch<<<n, kTellThreads, 0, s>>>(sel, t.k, t.st, t.y, t.params, t.loss, op == 1);
+    if (op == 1 || op == 3 || op == 4)
+        k_cma_tell_batch<<<n, kTellThreads, 0, s>>>(sel, t.k, t.st, t.y, t.params, t.loss, op == 4 ? 2 : op == 1);
     if (op == 2) k_cma_finish_batch<<<n, 32, 0, s>>>(sel, t.k, t.st, t.pose);
     return cudaGetLastError();
 }

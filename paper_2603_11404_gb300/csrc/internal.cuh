@@ -214,8 +214,10 @@ struct BatchTables {
     int *ninst = nullptr;
 };
 // op 0 reset from the estimate, 1 update, 2 frame epilogue, 3 update without
-// the square roots (a frame's last generation); one block per selected
-// instance (sel[n] device indices, or NULL for instances 0..n-1)
+// the square roots (a frame's last generation), 4 update where a selected
+// entry with kSelNoSqrt set leaves them out; one block per selected instance
+// (sel[n] device indices, or NULL for instances 0..n-1)
+constexpr int kSelNoSqrt = 1 << 30;
 cudaError_t launch_cma_batch(int op, int n, const int *sel, const BatchTables &t, cudaStream_t s);
 
 static_assert(sizeof(EvalArgs) % 16 == 0, "batched launches copy EvalArgs in 16-byte pieces");

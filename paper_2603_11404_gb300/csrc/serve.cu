@@ -101,6 +101,9 @@ struct trk_server {
     double t_ref = 0.0;
     LaunchCfg lc{};
     int max_clusters = 0;
+    // light ticks: the widest cluster (up to 8 CTAs per candidate) whose
+    // persistent grid holds every candidate of the tick at once
+    int max_clusters_by_size[9] = {};
     std::vector<trk_frame_result> completed;
     int rr = 0;                // round-robin start for admission
     int n_active = 0;
@@ -197,11 +200,19 @@ trk_status reconfigure(trk_server *v)
             max_inst = std::max(max_inst, v->cs[i].es->t->ch.n_inst);
         }
     if (v->lc.threads < 32 * max_inst) return sfail(TRK_EINVAL, "threads too few for two instruments");
-    int maxc = 0;
+    int maxc = 0, maxw = 0;
     SCU(prepare_eval_batch(smem, v->lc.cluster, v->lc.threads, &maxc), "server launch shape");
     if (maxc <= 0) return sfail(TRK_EINVAL, "launch shape does not fit on the device");
     v->lc.smem = smem;
     v->max_clusters = maxc;
+    // a light tick (few admitted frames) runs its candidates on as many CTAs
+    // each as lets them all run at once: its latency is one candidate's, which
+    // more CTAs per candidate shorten
+    for (int c = 0; c <= 8; ++c) v->max_clusters_by_size[c] = 0;
+    for (int c = v->lc.cluster + 1; c <= 8; ++c) {
+        SCU(prepare_eval_batch(smem, c, v->lc.threads, &maxw), "server wide launch shape");
+        v->max_clusters_by_size[c] = maxw;
+    }
     return TRK_OK;
 }
 
@@ -455,8 +466,14 @@ trk_status server_step(trk_server *v, int32_t *n_active_out, int32_t *n_queued_o
         for (int c = 0; c < v->cs[i].es->lam; ++c) items[n_items++] = make_int2(i, c);
     for (int i : admitted) sel_new[n_new++] = i;
     for (int i : act) {
-        sel_all[n_all++] = i;
-        if (v->cs[i].gen + 1 == v->cs[i].gens) sel_done[n_done++] = i;
+        // a frame's last generation: its update leaves out the square roots
+        // (the next frame restarts from C = I)
+        const bool last = v->cs[i].gen + 1 == v->cs[i].gens;
+        sel_all[n_all++] = last ? (i | kSelNoSqrt) : i;
+        if (last) {
+            sel_done[n_done++] = i;
+            v->cs[i].es->sqrt_pending = true;
+        }
     }
     char *dev = static_cast<char *>(tk.dev);
     int2 *d_items = reinterpret_cast<int2 *>(dev);
@@ -484,10 +501,16 @@ trk_status server_step(trk_server *v, int32_t *n_active_out, int32_t *n_queued_o
     }
     SCU(launch_cma_batch(0, n_new, d_new, v->tb, s), "reset");
     SCU(cudaMemsetAsync(v->next_item, 0, sizeof(unsigned), s), "queue reset");
-    SCU(launch_eval_batch(v->descs, nullptr, d_items, n_items, v->next_item, v->lc,
-                          std::min(v->max_clusters, n_items), s),
-        "fitness");
-    SCU(launch_cma_batch(1, n_all, d_all, v->tb, s), "update");
+    LaunchCfg lc = v->lc;
+    int n_clusters = std::min(v->max_clusters, n_items);
+    for (int c = 8; c > v->lc.cluster; --c)
+        if (n_items <= v->max_clusters_by_size[c]) {
+            lc.cluster = c;
+            n_clusters = n_items;
+            break;
+        }
+    SCU(launch_eval_batch(v->descs, nullptr, d_items, n_items, v->next_item, lc, n_clusters, s), "fitness");
+    SCU(launch_cma_batch(4, n_all, d_all, v->tb, s), "update");
     SCU(launch_cma_batch(2, n_done, d_done, v->tb, s), "epilogue");
     float *res = reinterpret_cast<float *>(static_cast<char *>(tk.pin) + tick_table_bytes(v));
     for (int k = 0; k < n_done; ++k) {
