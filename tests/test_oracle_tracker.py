@@ -22,3 +22,73 @@ def test_c1_fit_reduces_xor():
         assert oracle.eval_population(sc, best[None], M)["xor"][0] == best_loss
         ratios.append(best_loss / max(x0, 1))
     assert np.median(ratios) < 0.3
+
+
+class _Recording(CMAES):
+    """The oracle CMA-ES, recording every reset mean and every population with its losses."""
+
+    def __init__(self, *a, **kw):
+        self.resets, self.history = [], []
+        super().__init__(*a, **kw)
+
+    def reset(self, mean_phys, sigma0=None):
+        self.resets.append(np.array(mean_phys, np.float64))
+        super().reset(mean_phys, sigma0)
+
+    def tell(self, loss):
+        self.history.append((self.params.copy(), np.asarray(loss).copy()))
+        return super().tell(loss)
+
+
+def test_frame_estimate_is_the_best_candidate_of_the_frame():
+    """Sec. III-A reading: the frame's estimate is the best candidate over its
+    generations, ties to the earlier generation and then the lower index --
+    checked against every population the frame evaluated, on a corrupted mask
+    whose 4-generation frame reaches its minimum XOR in two generations (so a
+    rule that let the later one win fails here)."""
+    sc = wl.make_scene("c1", "c1")
+    rng = np.random.default_rng(9)
+    gt = wl.sample_state(rng, sc.K)
+    M = wl.corrupt_mask(oracle.render(sc, gt), rng)
+    init = wl.population_around(rng, gt, 1)[0].astype(np.float64)
+    for gens in (1, 4):
+        es = _Recording(9, 16, init, wl.default_scales(9), sigma0=1.0, seed=11)
+        best, best_loss = track_frame(es, sc, M, gens, wl.LOSS_XOR, init)
+        assert len(es.history) == gens
+        losses = np.concatenate([l for _, l in es.history])
+        params = np.concatenate([p for p, _ in es.history])
+        first = int(np.argmin(losses))  # argmin returns the first minimum: earlier generation, lower index
+        assert best_loss == losses.min()
+        assert np.array_equal(best.astype(np.float32), params[first])
+        assert oracle.eval_population(sc, params[first][None].astype(np.float64), M)["xor"][0] == best_loss
+        if gens == 4:  # the tie this case was chosen for
+            assert sum(bool((l == best_loss).any()) for _, l in es.history) == 2
+
+
+def test_frames_warm_start_from_the_previous_estimate_and_joint_readings():
+    """Sec. III-A: every frame restarts the search around the previous frame's
+    estimate (Sigma = I, sigma = sigma0, zero paths: Sec. IV), and joint
+    readings, when given, replace the joints of that mean through the forward
+    cosine map."""
+    sc = wl.make_scene("c1", "c1")
+    rng = np.random.default_rng(8)
+    traj = wl.sinusoidal_trajectory(rng, wl.sample_state(rng, sc.K), 3)
+    es = _Recording(9, 16, traj[0], wl.default_scales(9), sigma0=0.7, seed=3)
+    est = traj[0]
+    reading = np.array([0.3, -0.2, 0.5])
+    for f in range(3):
+        M = oracle.render(sc, traj[f])
+        prev = np.array(est, np.float64)
+        est, _ = track_frame(es, sc, M, 2, wl.LOSS_XOR, prev, joint_reading=reading if f == 2 else None)
+        start = es.resets[-1]
+        if f < 2:
+            assert np.array_equal(start, prev)
+        else:
+            assert np.array_equal(start[:6], prev[:6])
+            for i in range(3):
+                assert start[6 + i] == oracle.qhat_from_q(reading[i], sc.q_lb[i], sc.q_ub[i])
+                assert abs(oracle.q_from_qhat(start[6 + i], sc.q_lb[i], sc.q_ub[i]) - reading[i]) < 1e-12
+    # the restart itself: C = I, sigma = sigma0 and zero paths
+    es.reset(est)
+    assert np.array_equal(es.C, np.eye(9)) and es.sigma == 0.7
+    assert not es.p_sigma.any() and not es.p_c.any() and es.gen == 0
