@@ -359,8 +359,7 @@ __device__ __forceinline__ void cma_tell_impl(const CmaConst &k, CmaState *st, c
     }
     for (int e = tid; e < dd; e += nt) {
         S.C[e] = st->C[e];
-        S.B[e] = st->B[e];
-        S.A2[e] = st->C_inv_half[e];
+        S.B[e] = st->C_inv_half[e];  // S.B: the eigen fallback reloads the basis itself
     }
     for (int r = tid; r < mu; r += nt) S.w[r] = k.w[r];
     __syncthreads();
@@ -405,51 +404,66 @@ __device__ __forceinline__ void cma_tell_impl(const CmaConst &k, CmaState *st, c
         S.part[part][i] = acc;
     }
     __syncthreads();
-    if (tid < d) {
-        double acc = 0.0;
-        for (int p = 0; p < 8; ++p) acc = __dadd_rn(acc, S.part[p][tid]);
-        S.yw[tid] = acc;
-    }
-    __syncthreads();
+    // The mean, the evolution paths and h_sigma in warp 0 (lanes = coordinates,
+    // d <= 32, shuffles instead of block barriers) while the other warps form
+    // the rank-mu sums: C <- decay C + c1 p_c p_c^T + c_mu sum w_r y_r y_r^T
+    // (block form: zero off-diagonal blocks), as 4 deterministic partial chains
+    // per upper-triangle entry in the (still unused) A, A2, V, V2 buffers
     const double sigma = st->sigma, cs = k.c_sigma, cc = k.c_c;
-    if (tid < d) {
-        double t = 0.0;
-        for (int j = 0; j < d; ++j) t = __fma_rn(S.A2[tid * d + j], S.yw[j], t);
-        double ps = __dadd_rn(__dmul_rn(1.0 - cs, st->p_sigma[tid]), __dmul_rn(k.ps_coef, t));
-        st->p_sigma[tid] = ps;
-        S.part[0][tid] = ps * ps;
-        double mn = __dadd_rn(st->m[tid], __dmul_rn(k.c_m * sigma, S.yw[tid]));
-        st->m[tid] = mn;
-        st->m_df[tid] = split_df(mn);
-    }
-    __syncthreads();
-    if (tid == 0) {
-        double n2 = 0.0;
-        for (int i = 0; i < d; ++i) n2 += S.part[0][i];
-        // h_sigma: |p_sigma| / sqrt(1 - (1 - c_sigma)^(2(g+1))) < (1.4 + 2/(n+1)) chi_n, compared squared
-        double pw = st->cs_pow * (1.0 - cs) * (1.0 - cs);
-        S.n2 = n2;
-        S.hs = (n2 < k.hs_thr2 * (1.0 - pw)) ? 1.0 : 0.0;
-        st->cs_pow = pw;
-    }
-    __syncthreads();
-    const double hs = S.hs;
-    if (tid < d) {
-        double v = __dadd_rn(__dmul_rn(1.0 - cc, st->p_c[tid]), __dmul_rn(hs * k.pc_coef, S.yw[tid]));
-        st->p_c[tid] = v;
-        S.pc[tid] = v;
-    }
-    __syncthreads();
-    // C <- decay C + c1 p_c p_c^T + c_mu sum w_r y_r y_r^T (block form: zero off-diagonal
-    // blocks); the rank-mu sum runs as 4 deterministic partial chains held in
-    // the (still unused) A, A2, V, V2 buffers
     const double c1 = k.c_1, cmu = k.c_mu;
-    const double decay = 1.0 + c1 * ((1.0 - hs) * cc * (2.0 - cc)) - c1 - cmu;
-    {
-        double *part4[4] = {S.A, S.A2, S.V, S.V2};
+    double *part4[4] = {S.A, S.A2, S.V, S.V2};
+    const int nup = d * (d + 1) / 2;  // entries (i, j), j >= i
+    const bool split = nt > 32;  // warp 0 takes the paths, the rest the rank-mu sums
+    if (tid < 32) {
+        const int lane = tid;
+        const bool on = lane < d;
+        double yw = 0.0;
+        if (on) {  // <y>_w from the 8 partial sums, as a fixed tree
+            const double a = __dadd_rn(S.part[0][lane], S.part[1][lane]), b = __dadd_rn(S.part[2][lane], S.part[3][lane]);
+            const double c = __dadd_rn(S.part[4][lane], S.part[5][lane]), e = __dadd_rn(S.part[6][lane], S.part[7][lane]);
+            yw = __dadd_rn(__dadd_rn(a, b), __dadd_rn(c, e));
+        }
+        // (C^(-1/2) <y>_w)_lane in three chains
+        double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+        for (int j = 0; j < d; j += 3) {
+            const double y0 = __shfl_sync(0xffffffffu, yw, j);
+            const double y1 = __shfl_sync(0xffffffffu, yw, j + 1 < d ? j + 1 : 0);
+            const double y2 = __shfl_sync(0xffffffffu, yw, j + 2 < d ? j + 2 : 0);
+            if (on) {
+                t0 = __fma_rn(S.B[lane * d + j], y0, t0);
+                if (j + 1 < d) t1 = __fma_rn(S.B[lane * d + j + 1], y1, t1);
+                if (j + 2 < d) t2 = __fma_rn(S.B[lane * d + j + 2], y2, t2);
+            }
+        }
+        const double t = __dadd_rn(__dadd_rn(t0, t1), t2);
+        double ps = 0.0;
+        if (on) {
+            ps = __dadd_rn(__dmul_rn(1.0 - cs, st->p_sigma[lane]), __dmul_rn(k.ps_coef, t));
+            st->p_sigma[lane] = ps;
+            const double mn = __dadd_rn(st->m[lane], __dmul_rn(k.c_m * sigma, yw));
+            st->m[lane] = mn;
+            st->m_df[lane] = split_df(mn);
+        }
+        double n2 = ps * ps;  // |p_sigma|^2 by a fixed butterfly
+        for (int o = 16; o; o >>= 1) n2 = __dadd_rn(n2, __shfl_xor_sync(0xffffffffu, n2, o));
+        // h_sigma: |p_sigma| / sqrt(1 - (1 - c_sigma)^(2(g+1))) < (1.4 + 2/(n+1)) chi_n, compared squared
+        const double pw = st->cs_pow * (1.0 - cs) * (1.0 - cs);
+        const double hs = (n2 < k.hs_thr2 * (1.0 - pw)) ? 1.0 : 0.0;
+        if (lane == 0) {
+            S.n2 = n2;
+            S.hs = hs;
+        }
+        __syncwarp();
+        if (lane == 0) st->cs_pow = pw;
+        if (on) {
+            const double v = __dadd_rn(__dmul_rn(1.0 - cc, st->p_c[lane]), __dmul_rn(hs * k.pc_coef, yw));
+            st->p_c[lane] = v;
+            S.pc[lane] = v;
+        }
+    }
+    if (!split || tid >= 32) {
         const int rchunk = (mu + 3) / 4;
-        const int nup = d * (d + 1) / 2;  // entries (i, j), j >= i
-        for (int e = tid; e < 4 * nup; e += nt) {
+        for (int e = split ? tid - 32 : tid; e < 4 * nup; e += split ? nt - 32 : nt) {
             const int pr = e / nup;
             int u = e - pr * nup, i = 0;
             while (u >= d - i) {  // row i holds d - i entries of the upper triangle
@@ -462,7 +476,11 @@ __device__ __forceinline__ void cma_tell_impl(const CmaConst &k, CmaState *st, c
             for (int r = pr * rchunk; r < r1; ++r) rmu = __fma_rn(S.w[r] * YSEL(r, i), YSEL(r, j), rmu);
             part4[pr][ij] = rmu;
         }
+    }
+    {
         __syncthreads();
+        const double hs = S.hs;
+        const double decay = 1.0 + c1 * ((1.0 - hs) * cc * (2.0 - cc)) - c1 - cmu;
         for (int e = tid; e < dd; e += nt) {
             int i = e / d, j = e - i * d;
             if (j < i) continue;
@@ -493,8 +511,6 @@ __device__ __forceinline__ void cma_tell_impl(const CmaConst &k, CmaState *st, c
     cma_sqrt_phases<DC>(k, st, S, tid, nt, true, sigma);
 }
 
-// C^(1/2), C^(-1/2) and the eigenbasis of C (S.C holds C, S.B the previous
-// basis), with the step-size update on the second warp when do_sigma.
 // C^(1/2) and C^(-1/2) by the coupled Newton-Schulz iteration for the matrix
 // square root (Higham, Functions of Matrices, SIAM 2008, Ch. 6): with
 // A = C / c, Y_0 = A and Z_0 = I,
@@ -593,10 +609,6 @@ __device__ __forceinline__ bool cma_sqrt_newton_schulz(const CmaConst &k, CmaSta
     }
     if (!done) {
         if (tid == 0) atomicOr(&st->warn, 2);
-        if constexpr (!kPacked) {  // the eigen path starts from the stored basis
-            for (int e = tid; e < dd; e += nt) S.B[e] = st->B[e];
-            __syncthreads();
-        }
         return false;
     }
     // outputs: C^(1/2) = sqrt(c) Y, C^(-1/2) = Z / sqrt(c) (sqrt(c) a power of
@@ -622,6 +634,9 @@ __device__ __forceinline__ bool cma_sqrt_newton_schulz(const CmaConst &k, CmaSta
     return true;
 }
 
+// C^(1/2) and C^(-1/2) of C (held in S.C), with the step-size update when
+// do_sigma: the Newton-Schulz iteration, else the eigen path (which also
+// stores the eigenbasis, its next warm start).
 template <int DC>
 __device__ __forceinline__ void cma_sqrt_phases(const CmaConst &k, CmaState *st, TellSmem &S, int tid, int nt,
                                                 bool do_sigma, double sigma)
@@ -634,6 +649,8 @@ __device__ __forceinline__ void cma_sqrt_phases(const CmaConst &k, CmaState *st,
             if (cma_sqrt_newton_schulz<DC>(k, st, S, tid, nt, do_sigma, sigma)) return;
         }
     }
+    for (int e = tid; e < dd; e += nt) S.B[e] = st->B[e];  // the previous basis: the warm start
+    __syncthreads();
 
     // ---- eigendecomposition, phase 1: one-sided (Hestenes) Jacobi in FP32 on
     //      the columns of X = C B (B = last generation's basis, a warm start),
