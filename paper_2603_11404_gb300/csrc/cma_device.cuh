@@ -386,11 +386,13 @@ __device__ __forceinline__ void cma_tell_impl(const CmaConst &k, CmaState *st, c
                 if (q < d) S.ysel[r * d + q] = yi[q];
     }
     __syncthreads();
-    if (tid == 0) {
-        int b = S.order[0];
-        if (S.sl[b] < st->best_loss) {
-            st->best_loss = S.sl[b];
-            for (int i = 0; i < d; ++i) st->best_x[i] = params[(size_t)b * d + i];
+    if (tid >= nt - 32) {  // the frame's best so far, on the last warp (the mean's partial sums start on the first)
+        const int lane = tid - (nt - 32), b = S.order[0];
+        const float prev = st->best_loss;
+        __syncwarp();
+        if (S.sl[b] < prev) {
+            for (int i = lane; i < d; i += 32) st->best_x[i] = params[(size_t)b * d + i];
+            if (lane == 0) st->best_loss = S.sl[b];
         }
     }
 #define YSEL(r, i) (staged ? S.ysel[(r) * d + (i)] : y[(size_t)S.order[r] * d + (i)])
@@ -581,13 +583,26 @@ __device__ __forceinline__ bool cma_sqrt_newton_schulz(const CmaConst &k, CmaSta
     __syncthreads();
     const int e2 = (int)S.part[1][0];
     const double ic = ldexp(1.0, -e2);
+    // the first step needs no products: Z_0 = I makes Z_0 Y_0 = Y_0 and
+    // T_0 Z_0 = T_0 exactly (bit for bit what the products would give)
+    bool open0 = false;
     for (int e = tid; e < dd; e += nt) {
-        Y[e] = __dmul_rn(C[e], ic);
-        Z[e] = (e / d == e % d) ? 1.0 : 0.0;
+        const int i = e / d, j = e - i * d;
+        const double y = __dmul_rn(C[e], ic);
+        const double r = ((i == j) ? 1.0 : 0.0) - y;
+        open0 |= !(fabs(r) < 1e-8);
+        const double t = ((i == j) ? 1.0 : 0.0) + 0.5 * r;
+        Y[e] = y;
+        T[e] = t;
+        Z[e] = t;
     }
+    bool done = !__syncthreads_or(open0);
+    for (int e = tid; e < dd; e += nt) Y2[e] = ns_dot<DC>(Y, T, e / d, e - (e / d) * d);
     __syncthreads();
-    int steps = 0;
-    bool done = false;
+    {
+        double *t = Y; Y = Y2; Y2 = t;
+    }
+    int steps = 1;
     while (!done && steps < kNsMaxSteps) {
         bool open = false;  // a residual entry at or above 1e-8 (or not a number)
         for (int e = tid; e < dd; e += nt) {
