@@ -111,6 +111,37 @@ def test_square_roots_stay_exact_on_an_ill_conditioned_quadratic(api):
     assert np.abs(Ch @ Ci - np.eye(9)).max() < 1e-12
 
 
+def test_indefinite_covariance_falls_back_to_the_eigen_path(api):
+    """A covariance with a negative eigenvalue (loaded through the save blob:
+    C at double offset 54 after the 24-byte header, the int warning word 12
+    bytes after the 1388 leading doubles) has no real square root: the
+    Newton-Schulz iteration does not converge (warning bit 1), the eigen path
+    takes over and clamps the eigenvalue (bit 0), and the state stays finite."""
+    sc = wl.make_scene("c1", "c1")
+    tr = api.Tracker(sc, lambda_max=16)
+    g = api.CMAES(tr, 16, np.ones(9), np.ones(9), sigma0=0.5, seed=4)
+    blob = bytearray(g.save())
+    rng = np.random.default_rng(5)
+    Q, _ = np.linalg.qr(rng.normal(size=(9, 9)))
+    w = np.ones(9)
+    w[4] = -2.0
+    C = (Q * w) @ Q.T
+    dbl = np.frombuffer(blob, np.float64, count=1388, offset=24).copy()
+    dbl[54:54 + 81] = (0.5 * (C + C.T)).ravel()
+    blob[24:24 + 8 * 1388] = dbl.tobytes()
+    g.load(bytes(blob))
+    P = g.ask().cpu().numpy()
+    g.tell(torch.from_numpy(np.sum(P.astype(np.float64) ** 2, axis=1).astype(np.float32)).cuda())
+    out = g.save()
+    warn = int(np.frombuffer(out, np.int32, count=1, offset=24 + 8 * 1388 + 12)[0])
+    assert warn & 2 and warn & 1, warn
+    dbl = np.frombuffer(out, np.float64, count=1388, offset=24)
+    assert np.isfinite(dbl[720:720 + 81]).all() and np.isfinite(dbl[1044:1044 + 81]).all()
+    st = g.state()
+    assert np.isfinite(st["m"]).all() and np.isfinite(st["C"]).all() and np.isfinite(st["sigma"])
+    assert np.isfinite(g.ask().cpu().numpy()).all()
+
+
 @pytest.mark.parametrize("d,lam", [(9, 64), (18, 32)])
 def test_device_normals_match_generator_definition(api, d, lam):
     """The kernel's Philox + FP32 Box-Muller draws equal the FP64 evaluation of
