@@ -72,11 +72,73 @@ static void binned_free(BinDev &b)
     b = BinDev{};
 }
 
+// The mesh as primitives for the fitness kernel: triangles that share an edge
+// with opposite directions (a consistently wound pair) become one record
+// (a, b, c, d) for the triangles (a, b, c) and (a, c, d); the rest stay single
+// (a, b, c, -1).  Greedy in mesh order: each triangle not yet taken pairs with
+// the first later free triangle across one of its edges, so the records keep
+// the mesh's order (neighbouring records draw neighbouring pixels).  Whether a
+// pair is drawn as one quadrilateral is decided per candidate on the device
+// (convexity of the projected corners); the union of pixels is the same.
+static std::vector<int4> pair_triangles(const std::vector<int4> &tris, long long T)
+{
+    struct DirEdge {
+        int u, v, t;
+    };
+    std::vector<DirEdge> edges;
+    edges.reserve((size_t)(3 * T));
+    for (int t = 0; t < (int)T; ++t) {
+        const int4 &r = tris[t];
+        edges.push_back({r.x, r.y, t});
+        edges.push_back({r.y, r.z, t});
+        edges.push_back({r.z, r.x, t});
+    }
+    auto key_less = [](const DirEdge &a, const DirEdge &b) {
+        return a.u != b.u ? a.u < b.u : (a.v != b.v ? a.v < b.v : a.t < b.t);
+    };
+    std::sort(edges.begin(), edges.end(), key_less);
+    std::vector<char> taken((size_t)std::max<long long>(T, 1), 0);
+    std::vector<int4> prims;
+    prims.reserve((size_t)T);
+    for (int t = 0; t < (int)T; ++t) {
+        if (taken[t]) continue;
+        taken[t] = 1;
+        const int c[3] = {tris[t].x, tris[t].y, tris[t].z};
+        int best = -1, best_k = 0;
+        for (int k = 0; k < 3; ++k) {
+            const int u = c[k], v = c[(k + 1) % 3];
+            // triangles holding the reverse edge v -> u
+            auto it = std::lower_bound(edges.begin(), edges.end(), DirEdge{v, u, 0}, key_less);
+            for (; it != edges.end() && it->u == v && it->v == u; ++it) {
+                const int o = it->t;
+                if (taken[o] || (best >= 0 && o >= best)) continue;
+                const int4 &r = tris[o];
+                const int w = r.x + r.y + r.z - u - v;  // the other triangle's third corner
+                if (w == c[0] || w == c[1] || w == c[2]) continue;  // a folded duplicate, not a pair
+                best = o;
+                best_k = k;
+            }
+        }
+        if (best < 0) {
+            prims.push_back(make_int4(c[0], c[1], c[2], -1));
+            continue;
+        }
+        taken[best] = 1;
+        // shared edge c[k] -> c[k+1]: rotate so that it is the closing edge c -> a
+        const int a0 = c[(best_k + 1) % 3], b0 = c[(best_k + 2) % 3], c0 = c[best_k];
+        const int4 &r = tris[best];
+        const int d0 = r.x + r.y + r.z - a0 - c0;
+        prims.push_back(make_int4(a0, b0, c0, d0));
+    }
+    return prims;
+}
+
 static void tracker_free(trk_tracker *t)
 {
     if (!t) return;
     cudaFree(t->verts);
     cudaFree(t->tris);
+    cudaFree(t->prims);
     cudaFree(t->snap);
     cudaFree(t->zero_mask);
     cudaFree(t->err);
@@ -267,9 +329,13 @@ trk_status tracker_create(const trk_link_mesh *meshes, int32_t n_meshes, const t
         vb += m.n_verts;
         tb += m.n_tris;
     }
+    std::vector<int4> hp = pair_triangles(ht, T);
+    t->P = (int)hp.size();
+    if (hp.empty()) hp.push_back(make_int4(0, 0, 0, -1));
     size_t snap_elems = (size_t)cfg->lambda_max * ch.n_inst * std::max<long long>(V, 1);
     if ((e = cudaMalloc(&t->verts, hv.size() * sizeof(float4))) != cudaSuccess ||
         (e = cudaMalloc(&t->tris, ht.size() * sizeof(int4))) != cudaSuccess ||
+        (e = cudaMalloc(&t->prims, hp.size() * sizeof(int4))) != cudaSuccess ||
         (e = cudaMalloc(&t->snap, snap_elems * sizeof(int2))) != cudaSuccess ||
         (e = cudaMalloc(&t->zero_mask, (size_t)cam.H * cam.Wq * 4)) != cudaSuccess ||
         (e = cudaMalloc(&t->err, sizeof(unsigned))) != cudaSuccess) {
@@ -279,6 +345,7 @@ trk_status tracker_create(const trk_link_mesh *meshes, int32_t n_meshes, const t
     }
     if ((e = cudaMemcpy(t->verts, hv.data(), hv.size() * sizeof(float4), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(t->tris, ht.data(), ht.size() * sizeof(int4), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(t->prims, hp.data(), hp.size() * sizeof(int4), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemset(t->zero_mask, 0, (size_t)cam.H * cam.Wq * 4)) != cudaSuccess ||
         (e = cudaMemset(t->err, 0, sizeof(unsigned))) != cudaSuccess) {
         tracker_free(t);
@@ -423,6 +490,8 @@ static trk_status eval_impl(trk_tracker *t, const float *params, int32_t lam, co
     a.tris = t->tris;
     a.V = t->V;
     a.T = t->T;
+    a.prims = t->prims;
+    a.P = t->P;
     a.params = params;
     a.d = t->d;
     a.lam = lam;
@@ -708,6 +777,8 @@ static trk_status fused_generation(trk_cmaes *es, const uint32_t *mask, int fini
     a.tris = t->tris;
     a.V = t->V;
     a.T = t->T;
+    a.prims = t->prims;
+    a.P = t->P;
     a.params = es->params;
     a.d = t->d;
     a.lam = es->lam;

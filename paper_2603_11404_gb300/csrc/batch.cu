@@ -199,6 +199,8 @@ trk_status batch_create(trk_tracker *const *trackers, trk_cmaes *const *optimise
         a.tris = t->tris;
         a.V = t->V;
         a.T = t->T;
+        a.prims = t->prims;
+        a.P = t->P;
         a.d = t->d;
         a.lam = b->lam[i];
         a.snap = b->snap + off;

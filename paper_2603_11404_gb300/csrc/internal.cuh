@@ -69,6 +69,11 @@ struct __align__(16) EvalArgs {
     const float4 *verts;   // [V] x, y, z, frame index (exact small float)
     const int4 *tris;      // [T] i0, i1, i2, 0
     int V, T;
+    // [P] the mesh as primitives: (a, b, c, d) is the pair of triangles (a, b, c)
+    // and (a, c, d) sharing the edge a-c, (a, b, c, -1) a single triangle; NULL
+    // in the index-checked launch, which draws tris[]
+    const int4 *prims;
+    int P, pad_p;
     const float *params;   // [lam * d]
     int d, lam;
     const uint32_t *mask;  // packed [H * Wq]
@@ -233,6 +238,8 @@ struct trk_tracker {
     int V = 0, T = 0, d = 0;
     float4 *verts = nullptr;
     int4 *tris = nullptr;
+    int4 *prims = nullptr;     // the mesh as quadrilateral pairs and single triangles (EvalArgs::prims)
+    int P = 0;
     int2 *snap = nullptr;       // scratch [lambda_max * n_inst * V]
     int raster = 0;             // TRK_RASTER_CLUSTER or TRK_RASTER_BINNED (resolved at create)
     trk::BinDev bin{};          // binned pipeline scratch (raster == TRK_RASTER_BINNED)

@@ -99,7 +99,267 @@ __device__ __forceinline__ void gather3(const int2 *sv, int4 tri, int2 &v0, int2
     if (kChecked && tri.w) v0.x = kSnapFlag;
 }
 
-template <bool kInlineFallback, bool kChecked = false>
+// Chunk tickets of phase 2: lane 0 takes the next chunk from the counter in
+// CTA 0's shared memory and broadcasts it.
+__device__ __forceinline__ int chunk_ticket(int *ctr, int lane)
+{
+    int v = 0;
+    if (lane == 0) v = atomicAdd(ctr, 1);
+    return __shfl_sync(0xffffffffu, v, 0);
+}
+
+__device__ __forceinline__ bool small_box(int spanx, int spany) { return spanx < 32 * 256 && spany < 64 * 256; }
+
+// One triangle of phase 2: drawn by this lane when small, otherwise deferred to
+// a whole warp through the CTA's list (entry `ent`).  Returns 1 when the
+// triangle is culled for a flagged vertex.
+template <bool kInlineFallback>
+__device__ __forceinline__ int draw_one_tri(int2 v0, int2 v1, int2 v2, int ent, const EvalArgs &a, uint32_t *bm,
+                                            int *big, int *sacc)
+{
+    TriSetup t;
+    const int st = tri_setup(v0, v1, v2, a.cam.W, a.cam.H, a.cull, t);
+    if (st == 1) {
+        if (small_box(t.spanx, t.spany)) {
+            raster_small(t, bm, a.cam.Wq);
+        } else {
+            // larger triangles wait for a whole warp.  If the list is full: the
+            // plain launch redraws every large primitive after the loop (raster
+            // code here would make its loop spill); the batched launch,
+            // compiled with more registers, draws the triangle in this lane
+            const int slot = atomicAdd(&sacc[4], 1);
+            if (slot < kBigListCap) big[slot] = ent;
+            else if constexpr (kInlineFallback) raster_serial(t, bm, a.cam.Wq);
+            else sacc[6] = 1;
+        }
+    }
+    return st == 2;
+}
+
+// Primitive t's record and snapped corners (written by other CTAs of the
+// cluster: read through L2).  A single triangle has w = -1 and no 4th corner.
+__device__ __forceinline__ int4 load_prim(const EvalArgs &a, int t)
+{
+    const int b = t >= a.P;  // instrument (at most 2): no division
+    return a.prims[t - b * a.P];
+}
+
+__device__ __forceinline__ void gather_prim(const EvalArgs &a, const int2 *snapc0, int t, int4 p, int2 &v0, int2 &v1,
+                                            int2 &v2, int2 &v3)
+{
+    const int2 *sv = snapc0 + (t >= a.P) * a.V;
+    v0 = __ldcg(sv + p.x);
+    v1 = __ldcg(sv + p.y);
+    v2 = __ldcg(sv + p.z);
+    if (p.w >= 0) v3 = __ldcg(sv + p.w);
+}
+
+// One primitive of phase 2 drawn by this lane: a convex quadrilateral in one
+// pass, anything else as its triangles; large ones are deferred to a whole
+// warp.  Returns the number of its triangles culled for a flagged vertex.
+template <bool kInlineFallback>
+__device__ __forceinline__ int draw_prim_lane(const EvalArgs &a, int t, int d, int2 v0, int2 v1, int2 v2, int2 v3,
+                                              uint32_t *bm, int *big, int *sacc)
+{
+    const int W = a.cam.W, H = a.cam.H, Wq = a.cam.Wq;
+    int st = 3, culled = 0;
+    if (d >= 0) {
+        QuadSetup q;
+        st = quad_setup(v0, v1, v2, v3, W, H, a.cull, q);
+        if (st == 1) {
+            if (small_box(q.spanx, q.spany)) {
+                raster_quad_small(q, bm, Wq);
+            } else {
+                const int slot = atomicAdd(&sacc[4], 1);
+                if (slot < kBigListCap) {
+                    big[slot] = 4 * t;
+                } else if constexpr (kInlineFallback) {
+                    TriSetup ts;
+                    if (tri_setup(v0, v1, v2, W, H, a.cull, ts) == 1) raster_serial(ts, bm, Wq);
+                    if (tri_setup(v0, v2, v3, W, H, a.cull, ts) == 1) raster_serial(ts, bm, Wq);
+                } else {
+                    sacc[6] = 1;
+                }
+            }
+        }
+    }
+    if (st == 3) {
+        culled += draw_one_tri<kInlineFallback>(v0, v1, v2, 4 * t + 1, a, bm, big, sacc);
+        if (d >= 0) culled += draw_one_tri<kInlineFallback>(v0, v2, v3, 4 * t + 2, a, bm, big, sacc);
+    }
+    return culled;
+}
+
+// Phase 2 over the tracker's primitive list (quadrilateral pairs and single
+// triangles, prims[] of EvalArgs).  A warp takes a chunk of 32 primitives
+// (one per lane) from the cluster's counter and takes the next chunk's ticket
+// while it draws: a warp holds at most one chunk beyond the one it draws, so
+// the warps of a cluster run out of work together.  Deferred-list entries are
+// 4 * primitive + part: part 0 the whole quadrilateral (its two triangles), 1
+// its first triangle (a, b, c), 2 its second (a, c, d).  Returns this
+// thread's count of triangles culled for a flagged vertex.
+template <bool kInlineFallback>
+__device__ __forceinline__ int draw_prims(const EvalArgs &a, cg::cluster_group &cluster, const int2 *snapc0, uint32_t *bm,
+                                          int *big, int *sacc, int lane, int warp, int nwarp)
+{
+    const int W = a.cam.W, H = a.cam.H, Wq = a.cam.Wq;
+    const int NP = a.ch.n_inst * a.P, V = a.V, P = a.P;
+    int culled = 0;
+    int *ctr = cluster.map_shared_rank(&sacc[5], 0);
+    int cur = chunk_ticket(ctr, lane);
+    while (cur * 32 < NP) {  // tickets of one warp increase: once past the end, done
+        int tk = 0;
+        if (lane == 0) tk = atomicAdd(ctr, 1);  // the next chunk, read after drawing this one
+        const int t = cur * 32 + lane;
+        if (t < NP) {
+            const int4 p = load_prim(a, t);
+            int2 v0, v1, v2, v3 = make_int2(0, 0);
+            gather_prim(a, snapc0, t, p, v0, v1, v2, v3);
+            culled += draw_prim_lane<kInlineFallback>(a, t, p.w, v0, v1, v2, v3, bm, big, sacc);
+        }
+        cur = __shfl_sync(0xffffffffu, tk, 0);
+    }
+    __syncthreads();
+    // deferred large primitives: a warp per triangle, int64 edges
+    const int nbig = min(sacc[4], kBigListCap);
+    for (int e = warp; e < nbig; e += nwarp) {
+        const int ent = big[e], t = ent >> 2, part = ent & 3;
+        const int b = t >= P;
+        const int4 p = a.prims[t - b * P];
+        const int2 *sv = snapc0 + b * V;
+        const int2 u0 = __ldcg(sv + p.x), u1 = __ldcg(sv + p.y), u2 = __ldcg(sv + p.z);
+        TriSetup ts;
+        if (part != 2 && tri_setup(u0, u1, u2, W, H, a.cull, ts) == 1) raster_warp(ts, bm, Wq, lane);
+        if (part != 1 && tri_setup(u0, u2, __ldcg(sv + p.w), W, H, a.cull, ts) == 1) raster_warp(ts, bm, Wq, lane);
+    }
+    if (!kInlineFallback && sacc[6]) {
+        // the list overflowed: every large primitive of the candidate, a warp
+        // per triangle (drawing twice is harmless under the union); a primitive
+        // counts as large exactly as in the loop above
+        for (int base = warp * 32; base < NP; base += nwarp * 32) {
+            const int tt = base + lane;
+            bool l1 = false, l2 = false;
+            if (tt < NP) {
+                const int b = tt >= P;
+                const int4 p = a.prims[tt - b * P];
+                const int2 *sv = snapc0 + b * V;
+                const int2 u0 = __ldcg(sv + p.x), u1 = __ldcg(sv + p.y), u2 = __ldcg(sv + p.z);
+                int st = 3;
+                if (p.w >= 0) {
+                    const int2 u3 = __ldcg(sv + p.w);
+                    QuadSetup q;
+                    st = quad_setup(u0, u1, u2, u3, W, H, a.cull, q);
+                    if (st == 1) l1 = l2 = !small_box(q.spanx, q.spany);
+                    if (st == 3) {
+                        TriSetup ts;
+                        l2 = tri_setup(u0, u2, u3, W, H, a.cull, ts) == 1 && !small_box(ts.spanx, ts.spany);
+                    }
+                }
+                if (st == 3) {
+                    TriSetup ts;
+                    l1 = tri_setup(u0, u1, u2, W, H, a.cull, ts) == 1 && !small_box(ts.spanx, ts.spany);
+                }
+            }
+            for (int part = 1; part <= 2; ++part)
+                for (unsigned mm = __ballot_sync(0xffffffffu, part == 1 ? l1 : l2); mm; mm &= mm - 1) {
+                    const int tu = __shfl_sync(0xffffffffu, tt, __ffs(mm) - 1);
+                    const int b = tu >= P;
+                    const int4 p = a.prims[tu - b * P];
+                    const int2 *sv = snapc0 + b * V;
+                    const int2 u0 = __ldcg(sv + p.x);
+                    const int2 u1 = __ldcg(sv + (part == 1 ? p.y : p.z));
+                    const int2 u2 = __ldcg(sv + (part == 1 ? p.z : p.w));
+                    TriSetup ts;
+                    if (tri_setup(u0, u1, u2, W, H, a.cull, ts) == 1) raster_warp(ts, bm, Wq, lane);
+                }
+        }
+    }
+    return culled;
+}
+
+// Phase 2 over plain triangles (tris[] of EvalArgs; the index-checked launch on
+// meshes in caller memory).  Deferred-list entries are triangle indices.
+template <bool kInlineFallback, bool kChecked>
+__device__ __forceinline__ int draw_tris(const EvalArgs &a, cg::cluster_group &cluster, const int2 *snapc, uint32_t *bm,
+                                      int *big, int *sacc, int lane, int warp, int nwarp)
+{
+    const int W = a.cam.W, H = a.cam.H, Wq = a.cam.Wq;
+    int culled = 0;
+    const int NT = a.ch.n_inst * a.T;
+    int *ctr = cluster.map_shared_rank(&sacc[5], 0);
+    int cur = chunk_ticket(ctr, lane), nx1 = chunk_ticket(ctr, lane), nx2 = chunk_ticket(ctr, lane);
+    int t0 = cur * 32 + lane, t1 = nx1 * 32 + lane;
+    int4 tri1 = make_int4(0, 0, 0, 0);
+    int b1 = 0;
+    int2 v0 = make_int2(0, 0), v1 = v0, v2 = v0;
+    if (t0 < NT) {
+        const int b0 = t0 >= a.T;  // instrument (at most 2): no division
+        gather3<kChecked>(snapc + b0 * a.V, load_tri<kChecked>(a, t0), v0, v1, v2);
+    }
+    if (t1 < NT) {
+        b1 = t1 >= a.T;
+        tri1 = load_tri<kChecked>(a, t1);
+    }
+    while (cur * 32 < NT) {
+        const int nx3 = chunk_ticket(ctr, lane);
+        int2 w0 = make_int2(0, 0), w1 = w0, w2 = w0;
+        if (t1 < NT) gather3<kChecked>(snapc + b1 * a.V, tri1, w0, w1, w2);
+        const int t2 = nx2 * 32 + lane;
+        int4 tri2 = make_int4(0, 0, 0, 0);
+        int b2 = 0;
+        if (t2 < NT) {
+            b2 = t2 >= a.T;
+            tri2 = load_tri<kChecked>(a, t2);
+        }
+        if (t0 < NT) culled += draw_one_tri<kInlineFallback>(v0, v1, v2, t0, a, bm, big, sacc);
+        cur = nx1;
+        t0 = t1;
+        v0 = w0;
+        v1 = w1;
+        v2 = w2;
+        nx1 = nx2;
+        t1 = t2;
+        tri1 = tri2;
+        b1 = b2;
+        nx2 = nx3;
+    }
+    __syncthreads();
+    const int nbig = min(sacc[4], kBigListCap);
+    for (int e = warp; e < nbig; e += nwarp) {
+        int tt = big[e];
+        int b = tt >= a.T;
+        int2 u0, u1, u2;
+        gather3<kChecked>(snapc + b * a.V, load_tri<kChecked>(a, tt), u0, u1, u2);
+        TriSetup t;
+        tri_setup(u0, u1, u2, W, H, a.cull, t);
+        raster_warp(t, bm, Wq, lane);
+    }
+    if (!kInlineFallback && sacc[6]) {  // the list overflowed: every large triangle of the candidate, a warp each (drawing twice is harmless)
+        for (int base = warp * 32; base < NT; base += nwarp * 32) {
+            const int tt = base + lane;
+            bool large = false;
+            TriSetup t;
+            if (tt < NT) {
+                const int b = tt >= a.T;
+                int2 u0, u1, u2;
+                gather3<kChecked>(snapc + b * a.V, load_tri<kChecked>(a, tt), u0, u1, u2);
+                large = tri_setup(u0, u1, u2, W, H, a.cull, t) == 1 && !small_box(t.spanx, t.spany);
+            }
+            for (unsigned mm = __ballot_sync(0xffffffffu, large); mm; mm &= mm - 1) {
+                const int src = __ffs(mm) - 1, tu = __shfl_sync(0xffffffffu, tt, src);
+                const int b = tu >= a.T;
+                int2 u0, u1, u2;
+                gather3<kChecked>(snapc + b * a.V, load_tri<kChecked>(a, tu), u0, u1, u2);
+                TriSetup u;
+                tri_setup(u0, u1, u2, W, H, a.cull, u);
+                raster_warp(u, bm, Wq, lane);
+            }
+        }
+    }
+    return culled;
+}
+
+template <bool kInlineFallback, bool kChecked = false, bool kQuads = true>
 __device__ __forceinline__ void eval_candidate(const EvalArgs &a, int c, const uint32_t *mask_override,
                                                bool fused_tell, bool dependent_launch)
 {
@@ -110,7 +370,7 @@ __device__ __forceinline__ void eval_candidate(const EvalArgs &a, int c, const u
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
     const int nI = a.ch.n_inst, nF = a.ch.n_frames;
-    const int W = a.cam.W, H = a.cam.H, Wq = a.cam.Wq;
+    const int H = a.cam.H, Wq = a.cam.Wq;
     const int nwords = H * Wq;
 
     extern __shared__ __align__(16) unsigned char smem[];
@@ -191,112 +451,14 @@ __device__ __forceinline__ void eval_candidate(const EvalArgs &a, int c, const u
     }
     cluster.sync();  // arrive.release / wait.acquire: the snapped vertices are visible cluster-wide
 
-    // ---- phase 2: triangles -> this CTA's bitmap.  Warps of the whole cluster
-    //      take chunks of 32 triangles (one per lane) from a counter in CTA 0's
-    //      shared memory, so the cluster finishes together whatever the
-    //      triangles cost; the bitmaps are OR-ed in phase 3, so which CTA draws a
-    //      triangle does not change the result.  Three chunks are in flight:
-    //      the next chunk's vertices, the one after's indices and a ticket ----
-    int culled = 0;
-    const int NT = nI * a.T;
-    {
-        int *ctr = cluster.map_shared_rank(&sacc[5], 0);
-        auto ticket = [&]() {
-            int v = 0;
-            if (lane == 0) v = atomicAdd(ctr, 1);
-            return __shfl_sync(0xffffffffu, v, 0);
-        };
-        // chunk being drawn (vertices loaded), next chunk (indices loaded), and
-        // the one after (ticket taken)
-        int cur = ticket(), nx1 = ticket(), nx2 = ticket();
-        int t0 = cur * 32 + lane, t1 = nx1 * 32 + lane;
-        int4 tri1 = make_int4(0, 0, 0, 0);
-        int b1 = 0;
-        int2 v0 = make_int2(0, 0), v1 = v0, v2 = v0;
-        if (t0 < NT) {
-            const int b0 = t0 >= a.T;  // instrument (at most 2): no division
-            gather3<kChecked>(snapc + b0 * a.V, load_tri<kChecked>(a, t0), v0, v1, v2);
-        }
-        if (t1 < NT) {
-            b1 = t1 >= a.T;
-            tri1 = load_tri<kChecked>(a, t1);
-        }
-        while (cur * 32 < NT) {  // tickets of one warp increase: once past the end, done
-            const int nx3 = ticket();
-            int2 w0 = make_int2(0, 0), w1 = w0, w2 = w0;
-            if (t1 < NT) gather3<kChecked>(snapc + b1 * a.V, tri1, w0, w1, w2);
-            const int t2 = nx2 * 32 + lane;
-            int4 tri2 = make_int4(0, 0, 0, 0);
-            int b2 = 0;
-            if (t2 < NT) {
-                b2 = t2 >= a.T;
-                tri2 = load_tri<kChecked>(a, t2);
-            }
-            if (t0 < NT) {
-                TriSetup t;
-                const int st = tri_setup(v0, v1, v2, W, H, a.cull, t);
-                if (st == 2) ++culled;
-                if (st == 1) {
-                    if (t.spanx < 32 * 256 && t.spany < 64 * 256) {
-                        raster_small(t, bm, Wq);
-                    } else {
-                        // larger triangles wait for a whole warp.  If the list is
-                        // full: the plain launch redraws every large triangle after
-                        // the loop (raster code here would make its loop spill); the
-                        // batched launch, compiled with more registers, draws the
-                        // triangle in this lane
-                        int slot = atomicAdd(&sacc[4], 1);
-                        if (slot < kBigListCap) big[slot] = t0;
-                        else if constexpr (kInlineFallback) raster_serial(t, bm, Wq);
-                        else sacc[6] = 1;
-                    }
-                }
-            }
-            cur = nx1;
-            t0 = t1;
-            v0 = w0;
-            v1 = w1;
-            v2 = w2;
-            nx1 = nx2;
-            t1 = t2;
-            tri1 = tri2;
-            b1 = b2;
-            nx2 = nx3;
-        }
-    }
-    __syncthreads();
-    const int nbig = min(sacc[4], kBigListCap);
-    for (int e = warp; e < nbig; e += nwarp) {
-        int tt = big[e];
-        int b = tt >= a.T;
-        int2 u0, u1, u2;
-        gather3<kChecked>(snapc + b * a.V, load_tri<kChecked>(a, tt), u0, u1, u2);
-        TriSetup t;
-        tri_setup(u0, u1, u2, W, H, a.cull, t);
-        raster_warp(t, bm, Wq, lane);
-    }
-    if (!kInlineFallback && sacc[6]) {  // the list overflowed: every large triangle of the candidate, a warp each (drawing twice is harmless)
-        for (int base = warp * 32; base < NT; base += nwarp * 32) {
-            const int tt = base + lane;
-            bool large = false;
-            TriSetup t;
-            if (tt < NT) {
-                const int b = tt >= a.T;
-                int2 u0, u1, u2;
-                gather3<kChecked>(snapc + b * a.V, load_tri<kChecked>(a, tt), u0, u1, u2);
-                large = tri_setup(u0, u1, u2, W, H, a.cull, t) == 1 && !(t.spanx < 32 * 256 && t.spany < 64 * 256);
-            }
-            for (unsigned mm = __ballot_sync(0xffffffffu, large); mm; mm &= mm - 1) {
-                const int src = __ffs(mm) - 1, tu = __shfl_sync(0xffffffffu, tt, src);
-                const int b = tu >= a.T;
-                int2 u0, u1, u2;
-                gather3<kChecked>(snapc + b * a.V, load_tri<kChecked>(a, tu), u0, u1, u2);
-                TriSetup u;
-                tri_setup(u0, u1, u2, W, H, a.cull, u);
-                raster_warp(u, bm, Wq, lane);
-            }
-        }
-    }
+    // ---- phase 2: primitives -> this CTA's bitmap.  Warps of the whole cluster
+    //      take chunks of 32 primitives (one per lane) from a counter in CTA 0's
+    //      shared memory, so the cluster finishes together whatever they cost;
+    //      the bitmaps are OR-ed in phase 3, so which CTA draws a primitive does
+    //      not change the result.  Three chunks are in flight: the next chunk's
+    //      vertices, the one after's indices and a ticket ----
+    int culled = kQuads ? draw_prims<kInlineFallback>(a, cluster, snapc, bm, big, sacc, lane, warp, nwarp)
+                        : draw_tris<kInlineFallback, kChecked>(a, cluster, snapc, bm, big, sacc, lane, warp, nwarp);
     cluster.sync();
 
     // ---- phase 3: OR the cluster's bitmaps over this CTA's band, count ----
@@ -391,7 +553,7 @@ __global__ void __launch_bounds__(256, 4) k_eval(EvalArgs a)
 // (eval_population_noalloc), whose indices the host cannot validate.
 __global__ void __launch_bounds__(256, 4) k_eval_checked(EvalArgs a)
 {
-    eval_candidate<false, true>(a, blockIdx.y, nullptr, false, false);
+    eval_candidate<false, true, false>(a, blockIdx.y, nullptr, false, false);
 }
 
 // Persistent batched evaluation: a fixed grid of clusters pulls (instance,

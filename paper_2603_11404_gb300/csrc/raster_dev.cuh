@@ -383,6 +383,118 @@ static __device__ void raster_serial(const TriSetup &t, uint32_t *bm, int Wq)
         }
 }
 
+// ----------------------------------------------------------------------------
+// Quadrilaterals: two mesh triangles T1 = (a, b, c) and T2 = (a, c, d) that share
+// the edge a-c.  The top-left rule covers a pixel centre p exactly when the
+// point p + (e, e^2), e -> 0+, lies strictly inside the triangle (for a
+// non-horizontal edge the x shift decides the side, for a horizontal one the y
+// shift).  That point never lies on the diagonal a-c, and when both triangles
+// have the same orientation and (a, b, c, d) is strictly convex, the open
+// quadrilateral minus the diagonal is the union of the two open triangles.  So
+// the pixels of the quadrilateral under the same rule on its four edges are
+// exactly the union of the two triangles' pixels: one set-up and one pass over
+// one bounding box instead of two.  Anything else (a fold at a silhouette edge,
+// a non-convex or degenerate pair, a flagged vertex) is drawn as two triangles.
+// ----------------------------------------------------------------------------
+struct QuadSetup {
+    int x[4], y[4];       // snapped corners, positive orientation
+    int j0, j1, i0, i1;   // pixel bbox clamped to the image
+    int spanx, spany;     // corner bbox extent in 1/256 px
+};
+
+// Twice the signed area of (p, q, r); exact in int32 when every coordinate
+// difference is below 2^15.
+__device__ __forceinline__ long long orient2(int2 p, int2 q, int2 r, bool narrow)
+{
+    if (narrow) return (long long)((q.x - p.x) * (r.y - p.y) - (r.x - p.x) * (q.y - p.y));
+    return (long long)(q.x - p.x) * (long long)(r.y - p.y) - (long long)(r.x - p.x) * (long long)(q.y - p.y);
+}
+
+// Returns 0 = nothing to draw (no pixel centre in the corners' clipped box, or
+// both triangles culled as back faces), 1 = draw the quadrilateral, 3 = draw the
+// two triangles separately (tri_setup on each; it also counts flagged ones).
+__device__ __forceinline__ int quad_setup(int2 a, int2 b, int2 c, int2 d, int W, int H, int cull, QuadSetup &q)
+{
+    if (a.x == kSnapFlag || b.x == kSnapFlag || c.x == kSnapFlag || d.x == kSnapFlag) return 3;
+    const int xmn = min(min(a.x, b.x), min(c.x, d.x)), xmx = max(max(a.x, b.x), max(c.x, d.x));
+    const int ymn = min(min(a.y, b.y), min(c.y, d.y)), ymx = max(max(a.y, b.y), max(c.y, d.y));
+    // each triangle's box lies inside this one: an empty box leaves both empty
+    q.j0 = max(0, (xmn + 255) >> 8);
+    q.j1 = min(W - 1, xmx >> 8);
+    q.i0 = max(0, (ymn + 255) >> 8);
+    q.i1 = min(H - 1, ymx >> 8);
+    if (q.j0 > q.j1 || q.i0 > q.i1) return 0;
+    q.spanx = xmx - xmn;
+    q.spany = ymx - ymn;
+    const bool narrow = q.spanx < (1 << 15) && q.spany < (1 << 15);
+    const long long A1 = orient2(a, b, c, narrow), A2 = orient2(a, c, d, narrow);
+    const long long Da = orient2(b, d, a, narrow), Dc = orient2(b, d, c, narrow);
+    // same non-zero orientation, and a, c strictly on opposite sides of b-d
+    const bool convex = ((A1 > 0 && A2 > 0) || (A1 < 0 && A2 < 0)) && ((Da > 0 && Dc < 0) || (Da < 0 && Dc > 0));
+    if (!convex) return 3;
+    if (cull && A1 > 0) return 0;
+    if (A1 < 0) {  // reverse the corner order: positive orientation
+        int2 t = b;
+        b = d;
+        d = t;
+    }
+    q.x[0] = a.x; q.y[0] = a.y;
+    q.x[1] = b.x; q.y[1] = b.y;
+    q.x[2] = c.x; q.y[2] = c.y;
+    q.x[3] = d.x; q.y[3] = d.y;
+    return 1;
+}
+
+// One thread, four int32 incremental edge functions (edge k from corner k to
+// corner k+1, the top-left bias as in raster_small_at).  The same bounds as the
+// triangle form: spanx < 32 px, spany < 64 px.
+__device__ __forceinline__ void raster_quad_small(const QuadSetup &q, uint32_t *bm, int Wq)
+{
+    int r[4], cs[4], rs[4];
+    const int Px = 256 * q.j0, Py = 256 * q.i0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int k1 = (k + 1) & 3;
+        const int dx = q.x[k1] - q.x[k], dy = q.y[k1] - q.y[k];
+        const int bias = (dy < 0 || (dy == 0 && dx > 0)) ? 0 : 1;
+        r[k] = dx * (Py - q.y[k]) - dy * (Px - q.x[k]) - bias;
+        cs[k] = dy * 256;
+        rs[k] = dx * 256;
+    }
+    const int jb = q.j0 & ~31;
+    const int off = q.j0 - jb;
+    const int nb = q.j1 - q.j0 + 1;  // 1..32
+    const bool one_word = off + nb <= 32;
+    uint32_t *row = bm + (size_t)q.i0 * Wq + (jb >> 5);
+    for (int i = q.i0; i <= q.i1; ++i) {
+        int a0 = r[0], a1 = r[1], a2 = r[2], a3 = r[3];
+        uint32_t bits = 0u;
+#pragma unroll 4
+        for (int n = 0; n < nb; ++n) {
+            bits = __funnelshift_l((uint32_t)(~(a0 | a1 | a2 | a3)), bits, 1);  // (bits << 1) | covered
+            a0 -= cs[0];
+            a1 -= cs[1];
+            a2 -= cs[2];
+            a3 -= cs[3];
+        }
+        if (bits) {
+            const uint32_t rb = __brev(bits) >> (32 - nb);  // pixel j0 at bit 0
+            if (one_word) {
+                atomicOr(row, rb << off);
+            } else {
+                const uint32_t lo = rb << off, hi = rb >> (32 - off);
+                if (lo) atomicOr(row, lo);
+                if (hi) atomicOr(row + 1, hi);
+            }
+        }
+        r[0] += rs[0];
+        r[1] += rs[1];
+        r[2] += rs[2];
+        r[3] += rs[3];
+        row += Wq;
+    }
+}
+
 // Camera-frame position of one vertex from its frame's projective rows (hi/lo
 // pairs), perspective division and snap: int2 (U, V) in 1/256 px, or the flag
 // value when the vertex is behind z_near or outside the guard band; uv gets

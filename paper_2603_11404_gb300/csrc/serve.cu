@@ -331,6 +331,8 @@ trk_status server_add_stream(trk_server *v, trk_cmaes *es, int32_t generations, 
     a.tris = t->tris;
     a.V = t->V;
     a.T = t->T;
+    a.prims = t->prims;
+    a.P = t->P;
     a.d = t->d;
     a.lam = es->lam;
     a.snap = c.snap;

@@ -363,3 +363,88 @@ def test_repeat_launches_deterministic(api):
     ref = tr.eval_population(P, Mp, counts=True)[1].clone()
     for _ in range(5):
         assert torch.equal(tr.eval_population(P, Mp, counts=True)[1], ref)
+
+
+def _lattice_quads(rng, W, H, n, z, fx, corner_px=True):
+    """n quadrilaterals, each two triangles (a, b, c), (a, c, d) sharing a-c,
+    with corners on pixel centres (or on the 1/256 px lattice near them), so
+    that edges and diagonals run through pixel centres: the top-left rule
+    decides many pixels on both the outer edges and the shared diagonal."""
+    verts, tris = [], []
+    for _ in range(n):
+        cu, cv = rng.integers(4, W - 4), rng.integers(4, H - 4)
+        pts = []
+        for ang in np.sort(rng.uniform(0, 2 * np.pi, 4)):
+            r = rng.integers(1, 6)
+            du, dv = np.round(r * np.cos(ang)), np.round(r * np.sin(ang))
+            if not corner_px:
+                du += rng.integers(-3, 4) / 256.0
+                dv += rng.integers(-3, 4) / 256.0
+            pts.append(((cu + du - W / 2) * z / fx, (cv + dv - H / 2) * z / fx, 0.0))
+        base = len(verts)
+        verts.extend(pts)
+        if rng.random() < 0.5:  # either diagonal, either winding
+            q = [base, base + 1, base + 2, base + 3]
+        else:
+            q = [base + 1, base + 2, base + 3, base]
+        if rng.random() < 0.5:
+            q = q[::-1]
+        tris.append([q[0], q[1], q[2]])
+        tris.append([q[0], q[2], q[3]])
+    return verts, tris
+
+
+@pytest.mark.parametrize("corner_px", [True, False])
+def test_quad_pairs_on_the_pixel_lattice(api, corner_px):
+    """Pairs of triangles drawn as one quadrilateral: corners, edges and shared
+    diagonals through pixel centres (corner_px) or 1/256 px beside them; convex
+    and non-convex pairs of both windings (a non-convex pair is drawn as two
+    triangles).  Bit-exact against the oracle's triangle-by-triangle union,
+    with and without back-face culling."""
+    W, H, fx, z = 96, 64, 100.0, 100.0
+    rng = np.random.default_rng(61 + corner_px)
+    verts, tris = _lattice_quads(rng, W, H, 400, z, fx, corner_px)
+    sc = tiny_scene(W, H, fx, verts, tris)
+    st = np.array([[0, 0, 0, 0, 0, z, 0, 0, 0], [0, 0, 0, 3.0 / 256, -5.0 / 256, z, 0, 0, 0]], np.float32)
+    M = random_mask(rng, H, W)
+    for cull in (False, True):
+        for cluster, threads in ((1, 32), (2, 128), (8, 256)):
+            _check_population(api, sc, st, M, cull=cull, cluster=cluster, threads=threads)
+
+
+def test_quad_pairs_folded_degenerate_and_flagged(api):
+    """Pairs that must not be drawn as one quadrilateral: the second triangle
+    folded back over the first (a silhouette edge seen from the side), the
+    fourth corner on the diagonal's line (a zero-area second triangle), a
+    repeated corner, and pairs with a corner behind the near plane (each
+    triangle then counts as culled on its own)."""
+    W, H, fx, z = 80, 60, 100.0, 100.0
+    rng = np.random.default_rng(67)
+    verts, tris = [], []
+    for k in range(300):
+        cu, cv = rng.uniform(-W / 2 + 6, W / 2 - 6), rng.uniform(-H / 2 + 6, H / 2 - 6)
+        a = np.array([cu, cv]); c = a + rng.uniform(-5, 5, 2); b = a + rng.uniform(-5, 5, 2)
+        kind = k % 4
+        if kind == 0:  # folded: d on b's side of a-c
+            d = b + 0.3 * (c - b) + rng.uniform(-0.5, 0.5, 2)
+        elif kind == 1:  # d on the line a-c, beyond c
+            d = a + 1.5 * (c - a)
+        elif kind == 2:  # d repeats b
+            d = b.copy()
+        else:  # a regular pair, one corner pushed behind the camera below
+            d = a + c - b
+        base = len(verts)
+        for p in (a, b, c, d):
+            zz = z
+            verts.append([p[0] * zz / fx, p[1] * zz / fx, 0.0])
+        if kind == 3 and k % 8 == 3:
+            verts[base + 3][2] = -150.0  # z = 100 - 150 < z_near
+        tris.append([base, base + 1, base + 2])
+        tris.append([base, base + 2, base + 3])
+    sc = tiny_scene(W, H, fx, verts, tris)
+    st = np.array([[0, 0, 0, 0, 0, z, 0, 0, 0], [0.01, -0.02, 0.03, 0.4, -0.3, z, 0, 0, 0]], np.float32)
+    M = random_mask(rng, H, W)
+    counts, _, _ = _check_population(api, sc, st, M)
+    assert (counts[:, 3] > 0).all()  # the flagged pairs were counted per triangle
+    _check_population(api, sc, st, M, cull=True)
+
