@@ -330,6 +330,13 @@ trk_status tracker_create(const trk_link_mesh *meshes, int32_t n_meshes, const t
         tb += m.n_tris;
     }
     std::vector<int4> hp = pair_triangles(ht, T);
+    // draw order: the reverse of the mesh's.  Instrument meshes list the links
+    // from the shaft to the jaws and the shaft from its far end, so the tip
+    // (the largest primitives on screen) is drawn first and the small far end
+    // is left for when the cluster's warps run out of work.  Within a link
+    // neighbouring primitives stay together, so a chunk's 32 lanes draw
+    // primitives of similar size.  Any order gives the same union.
+    std::reverse(hp.begin(), hp.end());
     t->P = (int)hp.size();
     if (hp.empty()) hp.push_back(make_int4(0, 0, 0, -1));
     size_t snap_elems = (size_t)cfg->lambda_max * ch.n_inst * std::max<long long>(V, 1);
