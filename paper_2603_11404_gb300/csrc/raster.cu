@@ -190,14 +190,32 @@ __device__ __forceinline__ int draw_prim_lane(const EvalArgs &a, int t, int d, i
     return culled;
 }
 
+// One deferred entry drawn by the whole warp into this CTA's bitmap: the
+// triangles of primitive ent / 4 (part 0 both, 1 the first, 2 the second), a
+// pixel per lane with int64 edge functions.
+__device__ __forceinline__ void draw_deferred(const EvalArgs &a, const int2 *snapc0, int ent, uint32_t *bm, int lane)
+{
+    const int W = a.cam.W, H = a.cam.H, Wq = a.cam.Wq;
+    const int t = ent >> 2, part = ent & 3;
+    const int b = t >= a.P;
+    const int4 p = a.prims[t - b * a.P];
+    const int2 *sv = snapc0 + b * a.V;
+    const int2 u0 = __ldcg(sv + p.x), u1 = __ldcg(sv + p.y), u2 = __ldcg(sv + p.z);
+    TriSetup ts;
+    if (part != 2 && tri_setup(u0, u1, u2, W, H, a.cull, ts) == 1) raster_warp(ts, bm, Wq, lane);
+    if (part != 1 && tri_setup(u0, u2, __ldcg(sv + p.w), W, H, a.cull, ts) == 1) raster_warp(ts, bm, Wq, lane);
+}
+
 // Phase 2 over the tracker's primitive list (quadrilateral pairs and single
 // triangles, prims[] of EvalArgs).  A warp takes a chunk of 32 primitives
 // (one per lane) from the cluster's counter and takes the next chunk's ticket
 // while it draws: a warp holds at most one chunk beyond the one it draws, so
 // the warps of a cluster run out of work together.  Deferred-list entries are
 // 4 * primitive + part: part 0 the whole quadrilateral (its two triangles), 1
-// its first triangle (a, b, c), 2 its second (a, c, d).  Returns this
-// thread's count of triangles culled for a flagged vertex.
+// its first triangle (a, b, c), 2 its second (a, c, d); they are drawn after
+// the cluster barrier that follows, shared out over the whole cluster
+// (draw_cluster_deferred).  Returns this thread's count of triangles culled
+// for a flagged vertex.
 template <bool kInlineFallback>
 __device__ __forceinline__ int draw_prims(const EvalArgs &a, cg::cluster_group &cluster, const int2 *snapc0, uint32_t *bm,
                                           int *big, int *sacc, int lane, int warp, int nwarp)
@@ -220,18 +238,6 @@ __device__ __forceinline__ int draw_prims(const EvalArgs &a, cg::cluster_group &
         cur = __shfl_sync(0xffffffffu, tk, 0);
     }
     __syncthreads();
-    // deferred large primitives: a warp per triangle, int64 edges
-    const int nbig = min(sacc[4], kBigListCap);
-    for (int e = warp; e < nbig; e += nwarp) {
-        const int ent = big[e], t = ent >> 2, part = ent & 3;
-        const int b = t >= P;
-        const int4 p = a.prims[t - b * P];
-        const int2 *sv = snapc0 + b * V;
-        const int2 u0 = __ldcg(sv + p.x), u1 = __ldcg(sv + p.y), u2 = __ldcg(sv + p.z);
-        TriSetup ts;
-        if (part != 2 && tri_setup(u0, u1, u2, W, H, a.cull, ts) == 1) raster_warp(ts, bm, Wq, lane);
-        if (part != 1 && tri_setup(u0, u2, __ldcg(sv + p.w), W, H, a.cull, ts) == 1) raster_warp(ts, bm, Wq, lane);
-    }
     if (!kInlineFallback && sacc[6]) {
         // the list overflowed: every large primitive of the candidate, a warp
         // per triangle (drawing twice is harmless under the union); a primitive
@@ -378,7 +384,9 @@ __device__ __forceinline__ void eval_candidate(const EvalArgs &a, int c, const u
     uint32_t *bm = reinterpret_cast<uint32_t *>(scr + nI * kComposeScratch);  // [H*Wq]
     float *sM = reinterpret_cast<float *>(bm + ((nwords + 3) & ~3));          // [nI*nF*24]
     int *big = reinterpret_cast<int *>(sM + nI * nF * 24);                    // [kBigListCap]
-    int *sacc = big + kBigListCap;  // [8]: s I m culled, big-list count, ticket counter, big-list overflow
+    // [8]: s I m culled, big-list count, chunk ticket counter, big-list
+    // overflow, deferred-entry ticket counter
+    int *sacc = big + kBigListCap;
     __shared__ int red[4][32];
     __shared__ float s_par[kMaxD];
     __shared__ float2 s_z[kMaxD];
@@ -460,6 +468,30 @@ __device__ __forceinline__ void eval_candidate(const EvalArgs &a, int c, const u
     int culled = kQuads ? draw_prims<kInlineFallback>(a, cluster, snapc, bm, big, sacc, lane, warp, nwarp)
                         : draw_tris<kInlineFallback, kChecked>(a, cluster, snapc, bm, big, sacc, lane, warp, nwarp);
     cluster.sync();
+    if (kQuads) {
+        // the large primitives deferred by every CTA of the cluster, shared out
+        // over all its warps: the tip of a coarse mesh close to the camera lands
+        // in a few chunks, and a CTA drawing its own list alone would hold the
+        // whole cluster up.  Entry e of the cluster is entry e - start(r) of
+        // CTA r's list (lists read through DSMEM, complete at the barrier above)
+        const int cnt = lane < K ? min(*cluster.map_shared_rank(&sacc[4], lane), kBigListCap) : 0;
+        int incl = cnt;
+        for (int o = 1; o < 8; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 7);
+        if (total > 0) {  // the same in every CTA: the barrier below is uniform
+            int *ctr = cluster.map_shared_rank(&sacc[7], 0);
+            for (int e = chunk_ticket(ctr, lane); e < total; e = chunk_ticket(ctr, lane)) {
+                const int r = __popc(__ballot_sync(0xffffffffu, lane < K && incl <= e));
+                const int start = __shfl_sync(0xffffffffu, incl - cnt, r);
+                const int ent = cluster.map_shared_rank(big, r)[e - start];
+                draw_deferred(a, snapc, ent, bm, lane);
+            }
+            cluster.sync();  // every deferred primitive drawn before the bitmaps are read
+        }
+    }
 
     // ---- phase 3: OR the cluster's bitmaps over this CTA's band, count ----
     const int per = (nwords + K - 1) / K;

@@ -448,3 +448,35 @@ def test_quad_pairs_folded_degenerate_and_flagged(api):
     assert (counts[:, 3] > 0).all()  # the flagged pairs were counted per triangle
     _check_population(api, sc, st, M, cull=True)
 
+
+
+def test_large_quads_deferred_over_the_cluster(api):
+    """Large quadrilaterals (boxes of 100-3000 px, many wider than 32 px, so
+    that they go to the deferred list and are drawn after the loop by warps of
+    every CTA of the cluster) mixed with records that draw nothing (off-screen
+    pairs); bit-exact against the oracle, with and without culling, on one CTA
+    and on a cluster of eight."""
+    W, H, fx, z = 160, 128, 100.0, 100.0
+    rng = np.random.default_rng(73)
+    verts, tris = [], []
+    for k in range(600):
+        if k % 3 == 2:  # a pair far off screen: nothing to draw
+            cu, cv, r = rng.uniform(-4 * W, -2 * W), rng.uniform(-H, H), 3.0
+        else:
+            cu, cv = rng.uniform(-W / 2, W / 2), rng.uniform(-H / 2, H / 2)
+            r = rng.choice([6.0, 12.0, 20.0, 28.0])
+        ang = np.sort(rng.uniform(0, 2 * np.pi, 4))
+        base = len(verts)
+        for t_ in ang:
+            verts.append([(cu + r * np.cos(t_)) * z / fx, (cv + r * np.sin(t_)) * z / fx, 0.0])
+        q = [base, base + 1, base + 2, base + 3]
+        if rng.random() < 0.5:
+            q = q[::-1]
+        tris.append([q[0], q[1], q[2]])
+        tris.append([q[0], q[2], q[3]])
+    sc = tiny_scene(W, H, fx, verts, tris)
+    st = np.array([[0, 0, 0, 0, 0, z, 0, 0, 0], [0.0, 0.0, 0.3, 2.0, -1.0, z, 0, 0, 0]], np.float32)
+    M = random_mask(rng, H, W)
+    for cull in (False, True):
+        for cluster, threads in ((1, 64), (8, 256)):
+            _check_population(api, sc, st, M, cull=cull, cluster=cluster, threads=threads)
