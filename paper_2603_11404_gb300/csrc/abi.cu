@@ -493,12 +493,7 @@ static trk_status eval_impl(trk_tracker *t, const float *params, int32_t lam, co
     EvalArgs a{};
     a.ch = t->ch;
     a.cam = t->cam;
-    a.verts = t->verts;
-    a.tris = t->tris;
-    a.V = t->V;
-    a.T = t->T;
-    a.prims = t->prims;
-    a.P = t->P;
+    apply_mesh(a, t);
     a.params = params;
     a.d = t->d;
     a.lam = lam;
@@ -780,12 +775,7 @@ static trk_status fused_generation(trk_cmaes *es, const uint32_t *mask, int fini
     EvalArgs a{};
     a.ch = t->ch;
     a.cam = t->cam;
-    a.verts = t->verts;
-    a.tris = t->tris;
-    a.V = t->V;
-    a.T = t->T;
-    a.prims = t->prims;
-    a.P = t->P;
+    apply_mesh(a, t);
     a.params = es->params;
     a.d = t->d;
     a.lam = es->lam;

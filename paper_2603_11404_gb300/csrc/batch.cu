@@ -195,12 +195,7 @@ trk_status batch_create(trk_tracker *const *trackers, trk_cmaes *const *optimise
         EvalArgs a{};
         a.ch = t->ch;
         a.cam = t->cam;
-        a.verts = t->verts;
-        a.tris = t->tris;
-        a.V = t->V;
-        a.T = t->T;
-        a.prims = t->prims;
-        a.P = t->P;
+        apply_mesh(a, t);
         a.d = t->d;
         a.lam = b->lam[i];
         a.snap = b->snap + off;

@@ -255,6 +255,18 @@ struct trk_tracker {
     const float *kp_obs = nullptr;
 };
 
+// The tracker's mesh into a launch's arguments: vertices, triangles and the
+// primitive records the fitness kernel draws.
+inline void apply_mesh(trk::EvalArgs &a, const trk_tracker *t)
+{
+    a.verts = t->verts;
+    a.tris = t->tris;
+    a.V = t->V;
+    a.T = t->T;
+    a.prims = t->prims;
+    a.P = t->P;
+}
+
 // The tracker's keypoint term into a launch's arguments.
 inline void apply_keypoints(trk::EvalArgs &a, const trk_tracker *t)
 {

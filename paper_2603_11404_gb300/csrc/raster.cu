@@ -687,6 +687,7 @@ cudaError_t launch_eval_checked(const EvalArgs &a, const LaunchCfg &cfg, cudaStr
 cudaError_t launch_eval(const EvalArgs &a, const LaunchCfg &cfg, cudaStream_t s)
 {
     if (a.lam == 0) return cudaSuccess;
+    if (!a.prims) return cudaErrorInvalidValue;  // k_eval draws the primitive records (apply_mesh)
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3(cfg.cluster, a.lam, 1);
     lc.blockDim = dim3(cfg.threads, 1, 1);

@@ -327,12 +327,7 @@ trk_status server_add_stream(trk_server *v, trk_cmaes *es, int32_t generations, 
     EvalArgs a{};
     a.ch = t->ch;
     a.cam = t->cam;
-    a.verts = t->verts;
-    a.tris = t->tris;
-    a.V = t->V;
-    a.T = t->T;
-    a.prims = t->prims;
-    a.P = t->P;
+    apply_mesh(a, t);
     a.d = t->d;
     a.lam = es->lam;
     a.snap = c.snap;

@@ -937,10 +937,7 @@ trk_status soft_refine(trk_cmaes *es, const uint32_t *mask_packed_dev, int32_t t
     EvalArgs a{};
     a.ch = t->ch;
     a.cam = t->cam;
-    a.verts = t->verts;
-    a.tris = t->tris;
-    a.V = t->V;
-    a.T = t->T;
+    apply_mesh(a, t);
     a.params = r->P;
     a.d = d;
     a.lam = top_k;

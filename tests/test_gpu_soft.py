@@ -113,6 +113,27 @@ def test_refine_improves_or_keeps_the_estimate(api):
     assert np.array_equal(pose.cpu().numpy(), st["best_x"])
 
 
+def test_refine_adopts_candidates_after_a_short_search(api):
+    """After a single generation from a displaced start the gradient steps
+    find better binary fitness for some seeds: the refined candidates are
+    scored with the same fitness kernel as the search (a refinement that could
+    never be adopted would pass the test above)."""
+    sc, tr, M, Mp, P = _case(api, "c1", "c1", 1, None, 53, 16)
+    tr2 = api.Tracker(sc, loss_kind=wl.LOSS_XOR, lambda_max=16)
+    adopted = 0
+    for seed in range(6):
+        es = api.CMAES(tr2, 16, P[seed].astype(np.float64), wl.default_scales(9), sigma0=1.0, seed=11 + seed)
+        es.track_frame(Mp, 1)
+        before = es.state()["best_loss"]
+        pose, picked = es.refine(Mp, top_k=8, steps=10, lr=0.05)
+        st = es.state()
+        if picked >= 0:
+            adopted += 1
+            assert st["best_loss"] < before
+            assert tr2.eval_population(pose[None].contiguous(), Mp).item() == st["best_loss"]
+    assert adopted > 0
+
+
 def test_soft_rejects_bad_arguments(api):
     from paper_2603_11404_gb300._abi import TrkError
     sc, tr, M, Mp, P = _case(api, "c1", "c1", 1, None, 61, 2)
