@@ -11,13 +11,17 @@
 //            with round-half-even; the snapped vertices go to an L2-resident
 //            scratch array.
 //   phase 2  after a cluster barrier the warps of all CTAs take chunks of 32
-//            triangles from a counter in CTA 0's shared memory until none
+//            primitive records (edge-sharing triangle pairs, drawn as convex
+//            quadrilaterals where the projected corners allow, else as their
+//            triangles) from a counter in CTA 0's shared memory until none
 //            are left: integer setup (orientation, top-left bias, bbox), then
-//            small triangles are rasterised by one thread each with int32
-//            incremental edge functions, larger ones by a whole warp with
-//            int64 edge functions and __ballot_sync coverage words.  Coverage
-//            is OR-ed into the CTA's own full-image bitmap in shared memory.
-//   phase 3  after a second cluster barrier CTA r ORs band r of all the
+//            small primitives are rasterised by one thread each with int32
+//            incremental edge functions; larger ones are deferred and, after
+//            a second cluster barrier, drawn by the warps of the whole
+//            cluster with int64 edge functions and __ballot_sync coverage
+//            words.  Coverage is OR-ed into the CTA's own full-image bitmap
+//            in shared memory.
+//   phase 3  after a further cluster barrier CTA r ORs band r of all the
 //            cluster's bitmaps through distributed shared memory, ANDs with
 //            the observed mask, popcounts, and the cluster's counts meet in
 //            CTA 0, which writes counts and loss.
@@ -213,9 +217,9 @@ __device__ __forceinline__ void draw_deferred(const EvalArgs &a, const int2 *sna
 // the warps of a cluster run out of work together.  Deferred-list entries are
 // 4 * primitive + part: part 0 the whole quadrilateral (its two triangles), 1
 // its first triangle (a, b, c), 2 its second (a, c, d); they are drawn after
-// the cluster barrier that follows, shared out over the whole cluster
-// (draw_cluster_deferred).  Returns this thread's count of triangles culled
-// for a flagged vertex.
+// the cluster barrier that follows, shared out over the whole cluster (in
+// eval_candidate).  Returns this thread's count of triangles culled for a
+// flagged vertex.
 template <bool kInlineFallback>
 __device__ __forceinline__ int draw_prims(const EvalArgs &a, cg::cluster_group &cluster, const int2 *snapc0, uint32_t *bm,
                                           int *big, int *sacc, int lane, int warp, int nwarp)
@@ -463,8 +467,7 @@ __device__ __forceinline__ void eval_candidate(const EvalArgs &a, int c, const u
     //      take chunks of 32 primitives (one per lane) from a counter in CTA 0's
     //      shared memory, so the cluster finishes together whatever they cost;
     //      the bitmaps are OR-ed in phase 3, so which CTA draws a primitive does
-    //      not change the result.  Three chunks are in flight: the next chunk's
-    //      vertices, the one after's indices and a ticket ----
+    //      not change the result ----
     int culled = kQuads ? draw_prims<kInlineFallback>(a, cluster, snapc, bm, big, sacc, lane, warp, nwarp)
                         : draw_tris<kInlineFallback, kChecked>(a, cluster, snapc, bm, big, sacc, lane, warp, nwarp);
     cluster.sync();
