@@ -443,7 +443,9 @@ trk_status batch_autotune(trk_batch *b, const float *const *params_dev, const ui
  * host; server_step admits waiting frames into free slots (one frame per
  * stream at a time, at most max_active in all) and enqueues one *tick*: one
  * CMA-ES generation of every admitted frame, their candidates evaluated
- * together in one persistent launch and their updates in one launch.  A frame
+ * together in one persistent launch in which the last CTA of each frame's
+ * candidates runs that frame's update (a tick with a single frame launches
+ * track_frame_device's fused per-frame kernel instead).  A frame
  * finishes after its stream's `generations` ticks; frames admitted later join
  * at the next tick.  Every frame is computed by the kernels of
  * track_frame_device, so its pose is bit-identical to tracking it alone.

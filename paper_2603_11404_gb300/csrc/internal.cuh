@@ -190,7 +190,7 @@ cudaError_t launch_project_keypoints(const EvalArgs &a, const float *states, int
 size_t tell_smem_bytes();
 cudaError_t launch_eval_batch(const EvalArgs *descs_dev, const uint32_t *const *masks_dev, const int2 *items_dev,
                               int n_items, unsigned *next_item_dev, const LaunchCfg &cfg, int n_clusters,
-                              cudaStream_t s);
+                              cudaStream_t s, const int *tell_last_dev = nullptr);
 cudaError_t prepare_eval_batch(size_t smem, int cluster, int threads, int *max_clusters);
 cudaError_t launch_pack_mask(const uint8_t *mask, uint32_t *packed, int W, int H, int Wq, cudaStream_t s);
 size_t eval_smem_bytes(const EvalArgs &a);

@@ -71,8 +71,10 @@ cudaError_t launch_project_keypoints(const EvalArgs &a, const float *states, int
 // ----------------------------------------------------------------------------
 
 // One candidate c of one evaluation (all CTAs of the cluster call it together).
-// mask_override replaces a.mask when not NULL (batched launches); fused_tell
-// lets the last CTA of the launch run the CMA-ES update (single-instance mode).
+// mask_override replaces a.mask when not NULL (batched launches).  A non-zero
+// tell_ctas is the number of CTAs that evaluate a's population in this launch:
+// the last of them to finish runs the CMA-ES update (and, when a.cma_finish is
+// set, the frame epilogue).
 // Consecutive fused generations are launched with programmatic stream
 // serialisation (see griddep_wait).
 // Triangle t's vertex indices.  kChecked (meshes in the caller's device memory,
@@ -371,7 +373,7 @@ __device__ __forceinline__ int draw_tris(const EvalArgs &a, cg::cluster_group &c
 
 template <bool kInlineFallback, bool kChecked = false, bool kQuads = true>
 __device__ __forceinline__ void eval_candidate(const EvalArgs &a, int c, const uint32_t *mask_override,
-                                               bool fused_tell, bool dependent_launch)
+                                               unsigned tell_ctas, bool dependent_launch)
 {
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
@@ -558,11 +560,11 @@ __device__ __forceinline__ void eval_candidate(const EvalArgs &a, int c, const u
             a.loss[c] = L;
         }
     }
-    if (a.cma_st && fused_tell) {  // the last CTA to finish updates the search distribution
+    if (a.cma_st && tell_ctas) {  // the last CTA to finish updates the search distribution
         if (tid == 0) {
             __threadfence();
             unsigned ticket = atomicAdd(a.cma_done, 1u);
-            s_last = (ticket == gridDim.x * gridDim.y - 1);
+            s_last = (ticket == tell_ctas - 1);
         }
         __syncthreads();
         if (s_last) {
@@ -581,44 +583,80 @@ __device__ __forceinline__ void eval_candidate(const EvalArgs &a, int c, const u
 __global__ void __launch_bounds__(256, 4) k_eval(EvalArgs a)
 {
     griddep_launch_dependents();
-    eval_candidate<false>(a, blockIdx.y, nullptr, true, true);
+    eval_candidate<false>(a, blockIdx.y, nullptr, gridDim.x * gridDim.y, true);
 }
 
 // The same with index checks: meshes in the caller's device memory
 // (eval_population_noalloc), whose indices the host cannot validate.
 __global__ void __launch_bounds__(256, 4) k_eval_checked(EvalArgs a)
 {
-    eval_candidate<false, true, false>(a, blockIdx.y, nullptr, false, false);
+    eval_candidate<false, true, false>(a, blockIdx.y, nullptr, 0u, false);
 }
 
 // Persistent batched evaluation: a fixed grid of clusters pulls (instance,
 // candidate) items from a queue (largest first) until it is empty.  CTA 0 of
 // each cluster takes the ticket and the others read it through DSMEM, so the
-// cluster stays in lockstep.  The CMA-ES update runs in a separate launch.
+// cluster stays in lockstep.  kTell (serving ticks): tell_last holds one flag
+// per instance (1 for a frame's last generation) and the last CTA of each
+// instance's items runs that instance's CMA-ES update, as k_eval does for one
+// instance; items and flags sit in mapped pinned host memory that the host
+// rewrites between ticks (read with ld.cv, never from a cached line), and the
+// cluster that draws the launch's last ticket leaves the queue counter at zero
+// for the next tick.  Without kTell the updates are a separate launch.
+template <bool kTell>
 __global__ void __launch_bounds__(256, 3) k_eval_batch(const EvalArgs *descs, const uint32_t *const *masks,
-                                                       const int2 *items, int n_items, unsigned *next_item)
+                                                       const int2 *items, int n_items, unsigned *next_item,
+                                                       const int *tell_last)
 {
     cg::cluster_group cluster = cg::this_cluster();
     __shared__ int s_item;
+    __shared__ int s_tick[3];  // kTell: the item and its instance's flag, read once by CTA 0's thread 0
     __shared__ __align__(16) EvalArgs s_args;  // this item's descriptor, read from shared memory
     for (;;) {
-        if (cluster.block_rank() == 0 && threadIdx.x == 0) s_item = (int)atomicAdd(next_item, 1u);
+        if (cluster.block_rank() == 0 && threadIdx.x == 0) {
+            s_item = (int)atomicAdd(next_item, 1u);
+            if (kTell && s_item < n_items) {
+                const int2 v = __ldcv(items + s_item);
+                s_tick[0] = v.x;
+                s_tick[1] = v.y;
+                s_tick[2] = __ldcv(tell_last + v.x);
+            }
+        }
         cluster.sync();
         const int it = *cluster.map_shared_rank(&s_item, 0);
+        int2 ic = make_int2(0, 0);
+        int last = 0;
+        if (kTell && it < n_items) {
+            const int *t0 = cluster.map_shared_rank(s_tick, 0);
+            ic = make_int2(t0[0], t0[1]);
+            last = t0[2];
+        }
         cluster.sync();  // every CTA has its ticket before CTA 0 takes the next
-        if (it >= n_items) break;
-        const int2 ic = items[it];
+        if (it >= n_items) {
+            // every cluster draws exactly one ticket past the items: the last of
+            // them is the launch's last atomic on the counter
+            if (kTell && cluster.block_rank() == 0 && threadIdx.x == 0 && it == n_items + (int)gridDim.y - 1)
+                *next_item = 0u;
+            break;
+        }
+        if (!kTell) ic = items[it];
         const int4 *src = reinterpret_cast<const int4 *>(descs + ic.x);
         int4 *dst = reinterpret_cast<int4 *>(&s_args);
         for (int i = threadIdx.x; i < (int)(sizeof(EvalArgs) / 16); i += blockDim.x) dst[i] = src[i];
         __syncthreads();
-        eval_candidate<true>(s_args, ic.y, masks ? masks[ic.x] : nullptr, false, false);
+        unsigned tell = 0;
+        if (kTell) {
+            if (threadIdx.x == 0) s_args.cma_finish = last;
+            __syncthreads();
+            tell = (unsigned)s_args.lam * gridDim.x;  // every CTA of every candidate of the instance
+        }
+        eval_candidate<true>(s_args, ic.y, masks ? masks[ic.x] : nullptr, tell, false);
     }
 }
 
 cudaError_t launch_eval_batch(const EvalArgs *descs_dev, const uint32_t *const *masks_dev, const int2 *items_dev,
                               int n_items, unsigned *next_item_dev, const LaunchCfg &cfg, int n_clusters,
-                              cudaStream_t s)
+                              cudaStream_t s, const int *tell_last_dev)
 {
     if (n_items == 0) return cudaSuccess;
     cudaLaunchConfig_t lc = {};
@@ -633,12 +671,16 @@ cudaError_t launch_eval_batch(const EvalArgs *descs_dev, const uint32_t *const *
     attr[0].val.clusterDim.z = 1;
     lc.attrs = attr;
     lc.numAttrs = 1;
-    return cudaLaunchKernelEx(&lc, k_eval_batch, descs_dev, masks_dev, items_dev, n_items, next_item_dev);
+    return tell_last_dev ? cudaLaunchKernelEx(&lc, k_eval_batch<true>, descs_dev, masks_dev, items_dev, n_items,
+                                              next_item_dev, tell_last_dev)
+                         : cudaLaunchKernelEx(&lc, k_eval_batch<false>, descs_dev, masks_dev, items_dev, n_items,
+                                              next_item_dev, tell_last_dev);
 }
 
 cudaError_t prepare_eval_batch(size_t smem, int cluster, int threads, int *max_clusters)
 {
-    cudaError_t e = ensure_smem_attr((const void *)k_eval_batch, smem);
+    cudaError_t e = ensure_smem_attr((const void *)k_eval_batch<false>, smem);
+    if (e == cudaSuccess) e = ensure_smem_attr((const void *)k_eval_batch<true>, smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3(cluster, 1, 1);
@@ -651,7 +693,13 @@ cudaError_t prepare_eval_batch(size_t smem, int cluster, int threads, int *max_c
     attr[0].val.clusterDim.z = 1;
     lc.attrs = attr;
     lc.numAttrs = 1;
-    return cudaOccupancyMaxActiveClusters(max_clusters, k_eval_batch, &lc);
+    // both forms (with and without the fused updates) must fit the shape
+    int with_tell = 0;
+    if ((e = cudaOccupancyMaxActiveClusters(max_clusters, k_eval_batch<false>, &lc)) != cudaSuccess ||
+        (e = cudaOccupancyMaxActiveClusters(&with_tell, k_eval_batch<true>, &lc)) != cudaSuccess)
+        return e;
+    *max_clusters = std::min(*max_clusters, with_tell);
+    return cudaSuccess;
 }
 
 size_t tell_smem_bytes() { return sizeof(TellSmem); }

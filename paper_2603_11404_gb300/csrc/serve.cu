@@ -7,9 +7,13 @@
 // advances every admitted frame by one CMA-ES generation:
 //
 //   uploads of newly admitted masks -> reset of their optimisers ->
-//   one persistent fitness launch over all admitted frames' candidates ->
-//   one launch with every admitted frame's CMA-ES update ->
-//   epilogue + pose download for the frames that ran their last generation
+//   one persistent fitness launch over all admitted frames' candidates, in
+//   which the last CTA of each frame's candidates runs that frame's CMA-ES
+//   update (and, after its last generation, the frame epilogue) ->
+//   pose download for the frames that ran their last generation
+//
+// A tick with a single frame in the slots runs the fused per-frame kernel
+// instead (the one track_frame_device launches, same arithmetic).
 //
 // so a frame that arrives while others are on the GPU joins at the next tick
 // and its work shares launches with theirs (iteration-level batching), and a
@@ -68,8 +72,9 @@ struct DoneRec {
 struct Tick {
     cudaEvent_t ev = nullptr;
     bool in_flight = false;
-    void *pin = nullptr;      // pinned: items, selections, then results
-    void *dev = nullptr;      // device: items, selections
+    void *pin = nullptr;      // mapped pinned: tick table, then results
+    void *pin_dev = nullptr;  // the device's address of pin
+    int *dev = nullptr;       // device: the streams admitted at this tick
     std::vector<DoneRec> done;
     std::vector<int> release; // staging buffers free once this tick has run
     double t_enqueue = 0.0;
@@ -89,8 +94,8 @@ struct trk_server {
     std::vector<CamStream> cs;
     std::vector<EvalArgs> hdescs;
     EvalArgs *descs = nullptr;
+    unsigned *queue = nullptr; // fitness queue counter: zero between ticks (the kernel leaves it so)
     BatchTables tb;
-    unsigned *next_item = nullptr;
     uint8_t *stage = nullptr;  // pinned [max_pending][stage_bytes]
     std::vector<int> free_bufs;
     Tick ring[kRing];
@@ -124,9 +129,12 @@ trk_status sfail(trk_status st, const char *why)
         if (e_ != cudaSuccess) return sfail(TRK_ECUDA, cudaGetErrorString(e_));    \
     } while (0)
 
-// Tick table layout (both pinned and device copies): items, then the three
-// selections; the pinned copy is followed by the results of finished frames.
-size_t tick_table_bytes(const trk_server *v) { return v->items_cap * sizeof(int2) + 3 * v->max_streams * sizeof(int); }
+// Tick table layout, in mapped pinned memory that the fitness launch reads in
+// place (no upload): the streams admitted at this tick, one last-generation
+// flag per stream, then the items; the results of finished frames follow.
+// Only the admitted streams are copied to the device, for the reset launch.
+size_t tick_items_offset(const trk_server *v) { return (2 * v->max_streams * sizeof(int) + 15) & ~(size_t)15; }
+size_t tick_table_bytes(const trk_server *v) { return tick_items_offset(v) + v->items_cap * sizeof(int2); }
 size_t tick_result_bytes(const trk_server *v) { return (size_t)v->max_streams * (TRK_MAX_D + 1) * sizeof(float); }
 
 void server_free(trk_server *v)
@@ -139,16 +147,12 @@ void server_free(trk_server *v)
         cudaFree(t.dev);
     }
     for (CamStream &c : v->cs) cudaFree(c.snap);
+    cudaFree(v->queue);
     cudaFree(v->descs);
     cudaFree(v->tb.k);
     cudaFree(v->tb.st);
-    cudaFree(v->tb.y);
-    cudaFree(v->tb.params);
-    cudaFree(v->tb.loss);
     cudaFree(v->tb.joint);
-    cudaFree(v->tb.pose);
     cudaFree(v->tb.ninst);
-    cudaFree(v->next_item);
     cudaFreeHost(v->stage);
     if (v->ref) cudaEventDestroy(v->ref);
     if (v->s) cudaStreamDestroy(v->s);
@@ -196,7 +200,7 @@ trk_status reconfigure(trk_server *v)
     int max_inst = 1;
     for (size_t i = 0; i < v->cs.size(); ++i)
         if (v->cs[i].open) {
-            smem = std::max(smem, eval_smem_bytes(v->hdescs[i]));
+            smem = std::max(smem, std::max(eval_smem_bytes(v->hdescs[i]), tell_smem_bytes()));
             max_inst = std::max(max_inst, v->cs[i].es->t->ch.n_inst);
         }
     if (v->lc.threads < 32 * max_inst) return sfail(TRK_EINVAL, "threads too few for two instruments");
@@ -253,20 +257,21 @@ trk_status server_create(int32_t max_active, int32_t max_streams, int32_t max_pe
     if ((e = cudaStreamCreateWithFlags(&v->s, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaEventCreate(&v->ref)) != cudaSuccess ||
         (e = cudaMalloc(&v->descs, sizeof(EvalArgs) * max_streams)) != cudaSuccess ||
+        (e = cudaMalloc(&v->queue, sizeof(unsigned))) != cudaSuccess ||
+        (e = cudaMemsetAsync(v->queue, 0, sizeof(unsigned), v->s)) != cudaSuccess ||
         (e = cudaMalloc(&v->tb.k, P)) != cudaSuccess || (e = cudaMalloc(&v->tb.st, P)) != cudaSuccess ||
-        (e = cudaMalloc(&v->tb.y, P)) != cudaSuccess || (e = cudaMalloc(&v->tb.params, P)) != cudaSuccess ||
-        (e = cudaMalloc(&v->tb.loss, P)) != cudaSuccess || (e = cudaMalloc(&v->tb.joint, P)) != cudaSuccess ||
-        (e = cudaMalloc(&v->tb.pose, P)) != cudaSuccess ||
+        (e = cudaMalloc(&v->tb.joint, P)) != cudaSuccess ||
         (e = cudaMalloc(&v->tb.ninst, sizeof(int) * max_streams)) != cudaSuccess ||
-        (e = cudaMalloc(&v->next_item, sizeof(unsigned))) != cudaSuccess ||
         (e = cudaMallocHost(&v->stage, v->stage_bytes * max_pending)) != cudaSuccess) {
         server_free(v);
         return sfail(e == cudaErrorMemoryAllocation ? TRK_ENOMEM : TRK_ECUDA, cudaGetErrorString(e));
     }
     for (Tick &t : v->ring) {
         if ((e = cudaEventCreate(&t.ev)) != cudaSuccess ||
-            (e = cudaMallocHost(&t.pin, tick_table_bytes(v) + tick_result_bytes(v))) != cudaSuccess ||
-            (e = cudaMalloc(&t.dev, tick_table_bytes(v))) != cudaSuccess) {
+            (e = cudaHostAlloc(&t.pin, tick_table_bytes(v) + tick_result_bytes(v), cudaHostAllocMapped)) !=
+                cudaSuccess ||
+            (e = cudaHostGetDevicePointer(&t.pin_dev, t.pin, 0)) != cudaSuccess ||
+            (e = cudaMalloc(&t.dev, sizeof(int) * max_streams)) != cudaSuccess) {
             server_free(v);
             return sfail(e == cudaErrorMemoryAllocation ? TRK_ENOMEM : TRK_ECUDA, cudaGetErrorString(e));
         }
@@ -342,19 +347,17 @@ trk_status server_add_stream(trk_server *v, trk_cmaes *es, int32_t generations, 
     a.cma_st = es->st;
     a.cma_y = es->y;
     a.cma_z = es->z;
+    a.cma_done = es->done;
+    a.cma_pose_out = es->pose;
     v->hdescs[id] = a;
-    const void *kp = es->k, *stp = es->st, *yp = es->y, *pp = es->params, *lp = es->loss, *pose = es->pose;
+    const void *kp = es->k, *stp = es->st;
     const void *jp = c.use_joint ? es->joint : nullptr;
     const int ni = t->ch.n_inst;
     const size_t o = sizeof(void *) * id;
     SCU(cudaMemcpyAsync(v->descs + id, &v->hdescs[id], sizeof(EvalArgs), cudaMemcpyHostToDevice, v->s), "desc");
     SCU(cudaMemcpyAsync((char *)v->tb.k + o, &kp, sizeof(void *), cudaMemcpyHostToDevice, v->s), "table");
     SCU(cudaMemcpyAsync((char *)v->tb.st + o, &stp, sizeof(void *), cudaMemcpyHostToDevice, v->s), "table");
-    SCU(cudaMemcpyAsync((char *)v->tb.y + o, &yp, sizeof(void *), cudaMemcpyHostToDevice, v->s), "table");
-    SCU(cudaMemcpyAsync((char *)v->tb.params + o, &pp, sizeof(void *), cudaMemcpyHostToDevice, v->s), "table");
-    SCU(cudaMemcpyAsync((char *)v->tb.loss + o, &lp, sizeof(void *), cudaMemcpyHostToDevice, v->s), "table");
     SCU(cudaMemcpyAsync((char *)v->tb.joint + o, &jp, sizeof(void *), cudaMemcpyHostToDevice, v->s), "table");
-    SCU(cudaMemcpyAsync((char *)v->tb.pose + o, &pose, sizeof(void *), cudaMemcpyHostToDevice, v->s), "table");
     SCU(cudaMemcpyAsync(v->tb.ninst + id, &ni, sizeof(int), cudaMemcpyHostToDevice, v->s), "table");
     SCU(cudaStreamSynchronize(v->s), "stream registration");  // the sources above are host stack values
     trk_status st = reconfigure(v);
@@ -454,33 +457,31 @@ trk_status server_step(trk_server *v, int32_t *n_active_out, int32_t *n_queued_o
     for (int i = 0; i < v->max_streams; ++i)
         if (v->cs[i].open && v->cs[i].active) act.push_back(i);
     std::stable_sort(act.begin(), act.end(), [&](int x, int y) { return v->cs[x].cost > v->cs[y].cost; });
-    int2 *items = static_cast<int2 *>(tk.pin);
-    int *sel_new = reinterpret_cast<int *>(static_cast<char *>(tk.pin) + v->items_cap * sizeof(int2));
-    int *sel_all = sel_new + v->max_streams;
-    int *sel_done = sel_all + v->max_streams;
-    int n_items = 0, n_new = 0, n_all = 0, n_done = 0;
+    char *pin = static_cast<char *>(tk.pin);
+    int *sel_new = reinterpret_cast<int *>(pin);
+    int *tell_last = sel_new + v->max_streams;
+    int2 *items = reinterpret_cast<int2 *>(pin + tick_items_offset(v));
+    int n_items = 0, n_new = 0, n_done = 0;
+    std::vector<int> sel_done(act.size());
     for (int i : act)
         for (int c = 0; c < v->cs[i].es->lam; ++c) items[n_items++] = make_int2(i, c);
     for (int i : admitted) sel_new[n_new++] = i;
     for (int i : act) {
         // a frame's last generation: its update leaves out the square roots
-        // (the next frame restarts from C = I)
+        // (the next frame restarts from C = I) and ends with the epilogue
         const bool last = v->cs[i].gen + 1 == v->cs[i].gens;
-        sel_all[n_all++] = last ? (i | kSelNoSqrt) : i;
+        tell_last[i] = last ? 1 : 0;
         if (last) {
             sel_done[n_done++] = i;
             v->cs[i].es->sqrt_pending = true;
         }
     }
-    char *dev = static_cast<char *>(tk.dev);
-    int2 *d_items = reinterpret_cast<int2 *>(dev);
-    int *d_new = reinterpret_cast<int *>(dev + v->items_cap * sizeof(int2));
-    int *d_all = d_new + v->max_streams;
-    int *d_done = d_all + v->max_streams;
+    // the fitness launch reads the items and flags where the host wrote them
+    const char *pd = static_cast<const char *>(tk.pin_dev);
+    const int *d_tell_last = reinterpret_cast<const int *>(pd) + v->max_streams;
+    const int2 *d_items = reinterpret_cast<const int2 *>(pd + tick_items_offset(v));
     cudaStream_t s = v->s;
-    SCU(cudaMemcpyAsync(d_items, items, sizeof(int2) * n_items, cudaMemcpyHostToDevice, s), "tick items");
-    SCU(cudaMemcpyAsync(d_new, sel_new, sizeof(int) * 3 * v->max_streams, cudaMemcpyHostToDevice, s),
-        "tick selections");
+    if (n_new) SCU(cudaMemcpyAsync(tk.dev, sel_new, sizeof(int) * n_new, cudaMemcpyHostToDevice, s), "selections");
     // uploads of the newly admitted frames
     for (int i : admitted) {
         CamStream &c = v->cs[i];
@@ -496,19 +497,28 @@ trk_status server_step(trk_server *v, int32_t *n_active_out, int32_t *n_queued_o
         tk.release.push_back(c.cur.buf);
         c.cur.buf = -1;
     }
-    SCU(launch_cma_batch(0, n_new, d_new, v->tb, s), "reset");
-    SCU(cudaMemsetAsync(v->next_item, 0, sizeof(unsigned), s), "queue reset");
-    LaunchCfg lc = v->lc;
-    int n_clusters = std::min(v->max_clusters, n_items);
-    for (int c = 8; c > v->lc.cluster; --c)
-        if (n_items <= v->max_clusters_by_size[c]) {
-            lc.cluster = c;
-            n_clusters = n_items;
-            break;
-        }
-    SCU(launch_eval_batch(v->descs, nullptr, d_items, n_items, v->next_item, lc, n_clusters, s), "fitness");
-    SCU(launch_cma_batch(4, n_all, d_all, v->tb, s), "update");
-    SCU(launch_cma_batch(2, n_done, d_done, v->tb, s), "epilogue");
+    SCU(launch_cma_batch(0, n_new, tk.dev, v->tb, s), "reset");
+    const trk_tracker *t1 = act.size() == 1 ? v->cs[act[0]].es->t : nullptr;
+    if (t1 && t1->raster == TRK_RASTER_CLUSTER) {
+        // one frame in the slots: the fused per-frame kernel of
+        // track_frame_device, in the tracker's own launch shape
+        EvalArgs a = v->hdescs[act[0]];
+        a.cma_finish = tell_last[act[0]];
+        LaunchCfg lc1 = t1->lc;
+        lc1.smem = std::max(lc1.smem, tell_smem_bytes());
+        SCU(launch_eval(a, lc1, s), "fitness and update");
+    } else {
+        LaunchCfg lc = v->lc;
+        int n_clusters = std::min(v->max_clusters, n_items);
+        for (int c = 8; c > v->lc.cluster; --c)
+            if (n_items <= v->max_clusters_by_size[c]) {
+                lc.cluster = c;
+                n_clusters = n_items;
+                break;
+            }
+        SCU(launch_eval_batch(v->descs, nullptr, d_items, n_items, v->queue, lc, n_clusters, s, d_tell_last),
+            "fitness and updates");
+    }
     float *res = reinterpret_cast<float *>(static_cast<char *>(tk.pin) + tick_table_bytes(v));
     for (int k = 0; k < n_done; ++k) {
         CamStream &c = v->cs[sel_done[k]];
