@@ -202,6 +202,10 @@ trk_status reconfigure(trk_server *v)
         if (v->cs[i].open) {
             smem = std::max(smem, std::max(eval_smem_bytes(v->hdescs[i]), tell_smem_bytes()));
             max_inst = std::max(max_inst, v->cs[i].es->t->ch.n_inst);
+            // single-frame ticks launch the tracker's fused kernel on this device
+            const trk_tracker *t = v->cs[i].es->t;
+            if (t->raster == TRK_RASTER_CLUSTER)
+                SCU(prepare_eval(std::max(t->lc.smem, tell_smem_bytes())), "fused kernel shared memory");
         }
     if (v->lc.threads < 32 * max_inst) return sfail(TRK_EINVAL, "threads too few for two instruments");
     int maxc = 0, maxw = 0;
