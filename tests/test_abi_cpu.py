@@ -62,3 +62,42 @@ def test_image_above_the_bitmap_limit_is_rejected(lib):
     with pytest.raises(_abi.TrkError) as e:
         api.Tracker(wl.make_scene("c1", "c1", K=K), lambda_max=4)
     assert e.value.status == TRK_EINVAL
+
+
+def test_server_and_batch_argument_checks(lib):
+    """The serving and batching constructors and the server calls check their
+    arguments before any device call: out-of-range sizes and launch shapes,
+    NULL handles and unknown streams return TRK_EINVAL with a reason."""
+    out = C.c_void_p()
+    good = dict(max_active=8, max_streams=8, max_pending=64, max_pixels=640 * 512, max_lambda=64, reserve=0,
+                cluster=0, threads=0)
+
+    def create(**kw):
+        a = dict(good, **kw)
+        return lib.server_create(a["max_active"], a["max_streams"], a["max_pending"], a["max_pixels"],
+                                 a["max_lambda"], a["reserve"], a["cluster"], a["threads"], C.byref(out))
+
+    for bad in (dict(max_active=0), dict(max_streams=0), dict(max_streams=4097), dict(max_pending=0),
+                dict(max_pending=65537), dict(max_pixels=0), dict(max_pixels=1280 * 1280 + 1),
+                dict(max_lambda=0), dict(reserve=-1), dict(cluster=9), dict(cluster=-1), dict(threads=48),
+                dict(threads=288)):
+        assert create(**bad) == TRK_EINVAL, bad
+        assert out.value is None
+        assert lib.tracker_last_error()
+    assert lib.server_create(8, 8, 64, 640 * 512, 64, 0, 0, 0, None) == TRK_EINVAL
+    sid = C.c_int32()
+    assert lib.server_add_stream(None, None, 5, 0, C.byref(sid)) == TRK_EINVAL
+    assert lib.server_remove_stream(None, 0) == TRK_EINVAL
+    m = (C.c_uint8 * 16)()
+    assert lib.server_submit(None, 0, m, None, 0, -1.0) == TRK_EINVAL
+    a, q = C.c_int32(), C.c_int32()
+    assert lib.server_step(None, C.byref(a), C.byref(q)) == TRK_EINVAL
+    assert lib.server_poll(None, None, 0, 0, C.byref(a)) == TRK_EINVAL
+    assert lib.server_destroy(None) == TRK_EINVAL
+    assert lib.batch_create(None, None, None, 1, 0, 0, C.byref(out)) == TRK_EINVAL
+    assert out.value is None
+    lam = (C.c_int32 * 1)(64)
+    trackers = (C.c_void_p * 1)()
+    assert lib.batch_create(trackers, None, lam, 0, 0, 0, C.byref(out)) == TRK_EINVAL
+    assert lib.batch_create(trackers, None, None, 1, 0, 0, C.byref(out)) == TRK_EINVAL
+    assert lib.batch_create(trackers, None, lam, 1, 0, 0, None) == TRK_EINVAL
